@@ -1,0 +1,190 @@
+/*
+ * lcs.h -- C ABI of the GB300 (sm_103a) DIST hot path of the Lu-Lin parallel
+ * LCS method, as implemented in "Parallel Longest Common SubSequence
+ * Analysis In Chapel" (arXiv 2309.09072).
+ *
+ * Problem (Sec. I, Sec. II-A, Fig. 1).  String a (length m) labels the rows
+ * and string b (length n) the columns of a grid graph with (m+1) x (n+1)
+ * vertices; right and down edges weigh 0 and the diagonal edge into vertex
+ * (r, c) weighs 1 iff a_r = b_c.  With top and bottom boundary vertices
+ * numbered 0..n,
+ *
+ *     DIST(i, j) = heaviest path from top vertex i to bottom vertex j
+ *                = LCS(a, b[i:j])                for j >= i,
+ *     DIST(i, j) = -infinity (the sentinel)      for j <  i,
+ *
+ * and LCS(a, b) = DIST(0, n).  The library builds DIST strip by strip (rows
+ * of a in groups of h), combines strips up a binary tree with the (max,+)
+ * product D(i, j) = max_k U(i, k) + L(k, j) (Sec. II-A, Sec. II-B-1) taken
+ * under the Monge bound K(i, j-1) <= K(i, j) <= K(i+1, j), and walks the
+ * leftmost maximisers K back down the tree to one LCS (Sec. II-C..II-E).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an lcs_status and never throws or aborts.
+ *  - Pointers named *_host are host pointers; all other buffer pointers are
+ *    DEVICE pointers on the context's device.  The caller owns every buffer
+ *    it passes; the library never frees caller memory.  The context owns its
+ *    workspace (device memory it allocates itself, within the budget given to
+ *    lcs_create).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device-only calls are asynchronous on that stream; calls that
+ *    return a value through a *_host pointer synchronise it first.
+ *  - Dense DIST matrices are (n+1) x ld, row-major: row i = top vertex i,
+ *    column j = bottom vertex j.  ld is in elements, ld >= n+1, ld times the
+ *    element size is a multiple of 16 bytes, and the base is 16-byte aligned.
+ *    The lower triangle (j < i) holds the sentinel INT32_MIN (LCS_I32) or
+ *    INT16_MIN (LCS_I16).
+ *  - Rows belong to the first string `a`.  The orientation is part of the
+ *    contract: it decides which of several optimal LCS strings is returned.
+ *  - Empty strings are legal: the length is 0 and DIST has 0 on and above
+ *    the diagonal.
+ *  - A context is not re-entrant: use one per host thread or serialise.
+ *  - Results are exact integers and independent of strip height, tile shape
+ *    and schedule: every maximiser is the smallest one (ties go to the lower
+ *    index, as the "<=" comparison of Algorithm 2 does).
+ */
+#ifndef LCS_GB300_H
+#define LCS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lcs_ctx lcs_ctx;
+
+typedef enum {
+    LCS_OK = 0,
+    LCS_EINVAL = 1,     /* an argument is out of range, misaligned or NULL      */
+    LCS_ENOMEM = 2,     /* the workspace would exceed the budget / cudaMalloc failed */
+    LCS_ETIMEOUT = 3,   /* a bounded device-side wait gave up                   */
+    LCS_ECUDA = 4,      /* a CUDA runtime call failed (details: lcs_last_error) */
+    LCS_EAGAIN = 5,     /* no room now: retry later (batch admission)           */
+    LCS_EOVERFLOW = 6   /* a result does not fit the requested type / capacity  */
+} lcs_status;
+
+typedef enum {
+    LCS_I32 = 0,        /* int32_t entries, sentinel INT32_MIN                  */
+    LCS_I16 = 1         /* int16_t entries, sentinel INT16_MIN; legal iff
+                           m < 32768 and n < 32768 (values <= min(m, n))        */
+} lcs_dtype;
+
+/* Counters of the last call on a context (lcs_get_stats). */
+typedef struct {
+    int64_t workspace_bytes;        /* device workspace currently held          */
+    int64_t peak_workspace_bytes;   /* high-water mark since lcs_create          */
+    int32_t strip_height;           /* h used by the last call                   */
+    int32_t strips;                 /* ceil(m / h)                               */
+    int32_t merges;                 /* (max,+) merges in the tree                */
+    int32_t tree_levels;            /* merge levels above the strips             */
+    int32_t kernel_launches;        /* kernels the last call launched            */
+    int32_t tile;                   /* merge tile edge (vertices)                */
+} lcs_stats;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the
+ * workspace (0 = 64 GiB).  No device memory is allocated until the first
+ * call that needs it.  *out receives the context.
+ * Errors: EINVAL (out NULL, bad device), ECUDA. */
+lcs_status lcs_create(lcs_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Free the workspace and the context (synchronises the device first). */
+lcs_status lcs_destroy(lcs_ctx *ctx);
+
+/* Static description of a status code. */
+const char *lcs_strerror(lcs_status status);
+
+/* Text of the last error recorded on ctx (a CUDA error string or the
+ * argument that failed validation); "" if none.  Never NULL. */
+const char *lcs_last_error(lcs_ctx *ctx);
+
+/* Rows per strip for later calls; 0 restores the automatic choice.  Legal
+ * values are 1..256.  The results do not depend on it (leftmost rule).
+ * Errors: EINVAL. */
+lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
+
+/* Counters of the last call (see lcs_stats).  Errors: EINVAL. */
+lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out);
+
+/* Synchronise `stream` and report device-side failures of earlier
+ * asynchronous calls on ctx (ETIMEOUT from a bounded wait, EOVERFLOW from a
+ * capacity check); clears the device error word.  Errors: ECUDA, ETIMEOUT,
+ * EOVERFLOW. */
+lcs_status lcs_sync(lcs_ctx *ctx, void *stream);
+
+/* DIST of one strip of h rows (Sec. II-B-3 for h = 1; Sec. II-B-1's matrix
+ * of a block of consecutive rows otherwise): dist(i, j) = LCS(a_strip,
+ * b[i:j]).  Each column step applies the prefix-max over the strip's rows
+ * F_j(r) = max(F_j(r-1), F_{j-1}(r), F_{j-1}(r-1) + [a_r = b_j]) to all h
+ * rows at once.  a_strip: h device bytes; b: n device bytes; dist: dense
+ * (n+1) x ld in `dtype`.  1 <= h <= 256 (values are at most h, so they fit
+ * either dtype).  Asynchronous.
+ * Errors: EINVAL (h out of range, n < 0, ld/alignment), ENOMEM, ECUDA. */
+lcs_status lcs_strip_dist(lcs_ctx *ctx, const uint8_t *a_strip, int32_t h,
+                          const uint8_t *b, int64_t n, lcs_dtype dtype,
+                          void *dist, int64_t ld, void *stream);
+
+/* (max,+) merge of the DIST of an upper strip U and a lower strip L over
+ * the same columns (Sec. II-A's split through a middle vertex, Sec. II-B-1's
+ * combination in its DIST form):
+ *     dist_out(i, j) = max_{i <= k <= j} dist_u(i, k) + dist_l(k, j),
+ * evaluated under the Monge bound (U and L must be DIST matrices of strips:
+ * unit steps and the Monge inequality; arbitrary matrices are not legal
+ * input).  argmax_out (nullable, dense int32, same ld) receives the smallest
+ * maximising k (-1 below the diagonal).  All matrices dense (n+1) x ld in
+ * `dtype`; dist_out may not alias the inputs.  Asynchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA; ETIMEOUT / EOVERFLOW via lcs_sync. */
+lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64_t n,
+                     lcs_dtype dtype, int64_t ld, void *dist_out, int32_t *argmax_out,
+                     void *stream);
+
+/* Full DIST of the whole grid: dist(i, j) = LCS(a, b[i:j]).  dist: dense
+ * (n+1) x ld in dtype (LCS_I16 needs m, n < 32768).  Asynchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+lcs_status lcs_dist(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    lcs_dtype dtype, void *dist, int64_t ld, void *stream);
+
+/* LCS length = DIST(0, n) (Sec. I).  Synchronises the stream and writes
+ * *out_len_host.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+lcs_status lcs_length(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                      int64_t *out_len_host, void *stream);
+
+/* One LCS: the letters of a on the leftmost heaviest path (Sec. II-C..II-E),
+ * found by walking the leftmost maximisers down the merge tree.  out_lcs:
+ * device buffer of cap >= min(m, n) bytes.  Synchronises the stream and
+ * writes *out_len_host (the number of letters written).
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW (cap too small). */
+lcs_status lcs_traceback(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                         uint8_t *out_lcs, int64_t cap, int64_t *out_len_host, void *stream);
+
+/* The whole hot path in one call: strips, merge tree, and any of
+ *   dist  (nullable): dense (n+1) x ld DIST in dtype;
+ *   out_lcs (nullable): the LCS letters (cap >= min(m, n) bytes);
+ *   cross (nullable): int32 device array of m+1 cross vertices v[0..m],
+ *        v[r] = leftmost column of the path in row r (Sec. II-C);
+ *   out_len_device (nullable): int64 device word receiving the length.
+ * Asynchronous (nothing is read back).  With every output NULL the call
+ * still builds the tree and leaves the length in an internal word.
+ * Errors: EINVAL, ENOMEM, ECUDA; ETIMEOUT / EOVERFLOW via lcs_sync. */
+lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                     lcs_dtype dtype, void *dist, int64_t ld,
+                     uint8_t *out_lcs, int64_t cap, int32_t *cross,
+                     int64_t *out_len_device, void *stream);
+
+/* lcs_solve on HOST buffers: copies a and b to the device, runs the whole
+ * path, copies the requested outputs back (dist_host: (n+1) x ld in dtype,
+ * lcs_host: cap bytes) and writes *out_len_host.  Host buffers should be
+ * pinned for full copy speed (pageable memory works, slower).  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW. */
+lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,
+                          const uint8_t *b_host, int64_t n, lcs_dtype dtype,
+                          void *dist_host, int64_t ld, uint8_t *lcs_host, int64_t cap,
+                          int64_t *out_len_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCS_GB300_H */

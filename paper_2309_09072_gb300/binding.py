@@ -1,0 +1,246 @@
+"""Thin ctypes binding of ``liblcs_gb300.so`` (declared in ``include/lcs.h``).
+
+Every function here has the name of the C entry point it calls and does
+argument marshalling only (torch tensors -> device pointers, sizes, strides,
+the current CUDA stream); every step of the computation runs in the library's
+CUDA kernels.  There is no fallback: if the library is missing or fails to
+load, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblcs_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lcs.h")
+
+LCS_OK, LCS_EINVAL, LCS_ENOMEM, LCS_ETIMEOUT, LCS_ECUDA, LCS_EAGAIN, LCS_EOVERFLOW = range(7)
+LCS_I32, LCS_I16 = 0, 1
+
+
+class LcsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s (status %d): %s" % (fn_strerror(status), status, message))
+        self.status = status
+
+
+class lcs_stats(ctypes.Structure):
+    _fields_ = [
+        ("workspace_bytes", ctypes.c_int64),
+        ("peak_workspace_bytes", ctypes.c_int64),
+        ("strip_height", ctypes.c_int32),
+        ("strips", ctypes.c_int32),
+        ("merges", ctypes.c_int32),
+        ("tree_levels", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the entry points declared in include/lcs.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lcs_[a-z_0-9]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (building it first if it is absent and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("liblcs_gb300.so is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        st = ctypes.c_int
+        sig = {
+            "lcs_create": ([ctypes.POINTER(vp), ctypes.c_int, sz], st),
+            "lcs_destroy": ([vp], st),
+            "lcs_strerror": ([st], ctypes.c_char_p),
+            "lcs_last_error": ([vp], ctypes.c_char_p),
+            "lcs_set_strip_height": ([vp, i32], st),
+            "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
+            "lcs_sync": ([vp, vp], st),
+            "lcs_strip_dist": ([vp, vp, i32, vp, i64, st, vp, i64, vp], st),
+            "lcs_merge": ([vp, vp, vp, i64, st, i64, vp, vp, vp], st),
+            "lcs_dist": ([vp, vp, i64, vp, i64, st, vp, i64, vp], st),
+            "lcs_length": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+            "lcs_traceback": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+            "lcs_solve": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, vp, vp, vp], st),
+            "lcs_solve_host": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def fn_strerror(status: int) -> str:
+    try:
+        return load().lcs_strerror(int(status)).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "status"
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_of(t) -> int:
+    import torch
+    if t.dtype == torch.int32:
+        return LCS_I32
+    if t.dtype == torch.int16:
+        return LCS_I16
+    raise ValueError("DIST tensors are int32 or int16")
+
+
+def _ld(t) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("DIST tensors are 2-D with unit column stride")
+    return int(t.stride(0))
+
+
+def _check(ctx, status):
+    if status != LCS_OK:
+        msg = load().lcs_last_error(ctx)
+        raise LcsError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------------ entry points
+def lcs_create(device: int = 0, mem_budget_bytes: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(None, load().lcs_create(ctypes.byref(ctx), int(device), int(mem_budget_bytes)))
+    return ctx
+
+
+def lcs_destroy(ctx) -> None:
+    _check(ctx, load().lcs_destroy(ctx))
+
+
+def lcs_strerror(status: int) -> str:
+    return load().lcs_strerror(int(status)).decode()
+
+
+def lcs_last_error(ctx) -> str:
+    return load().lcs_last_error(ctx).decode()
+
+
+def lcs_set_strip_height(ctx, h: int) -> None:
+    _check(ctx, load().lcs_set_strip_height(ctx, int(h)))
+
+
+def lcs_get_stats(ctx) -> dict:
+    s = lcs_stats()
+    _check(ctx, load().lcs_get_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def lcs_sync(ctx, stream=None) -> None:
+    _check(ctx, load().lcs_sync(ctx, _stream(stream)))
+
+
+def lcs_strip_dist(ctx, a_strip, b, dist, stream=None) -> None:
+    """dist[i, j] = LCS(a_strip, b[i:j]) (dense (n+1) x ld int32/int16)."""
+    _check(ctx, load().lcs_strip_dist(ctx, _ptr(a_strip), int(a_strip.numel()), _ptr(b), int(b.numel()),
+                                      _dtype_of(dist), _ptr(dist), _ld(dist), _stream(stream)))
+
+
+def lcs_merge(ctx, dist_u, dist_l, dist_out, argmax_out=None, stream=None) -> None:
+    """dist_out[i, j] = max_k dist_u[i, k] + dist_l[k, j]; argmax_out = smallest k."""
+    n = dist_u.shape[0] - 1
+    _check(ctx, load().lcs_merge(ctx, _ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), _ld(dist_u),
+                                 _ptr(dist_out), _ptr(argmax_out), _stream(stream)))
+
+
+def lcs_dist(ctx, a, b, dist, stream=None) -> None:
+    _check(ctx, load().lcs_dist(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _dtype_of(dist),
+                                _ptr(dist), _ld(dist), _stream(stream)))
+
+
+def lcs_length(ctx, a, b, stream=None) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load().lcs_length(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()),
+                                  ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def lcs_traceback(ctx, a, b, out_lcs, stream=None) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load().lcs_traceback(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(out_lcs),
+                                     int(out_lcs.numel()), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def lcs_solve(ctx, a, b, dist=None, out_lcs=None, cross=None, out_len=None, stream=None) -> None:
+    """Asynchronous whole path; any output may be None (see lcs.h)."""
+    dtype = _dtype_of(dist) if dist is not None else LCS_I32
+    ld = _ld(dist) if dist is not None else 0
+    cap = int(out_lcs.numel()) if out_lcs is not None else 0
+    _check(ctx, load().lcs_solve(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), dtype, _ptr(dist), ld,
+                                 _ptr(out_lcs), cap, _ptr(cross), _ptr(out_len), _stream(stream)))
+
+
+def lcs_solve_host(ctx, a_host, b_host, dist_host=None, lcs_host=None, dtype=LCS_I32, stream=None) -> int:
+    """Whole path on host (ideally pinned) tensors; returns the LCS length."""
+    out = ctypes.c_int64()
+    if dist_host is not None:
+        dtype = _dtype_of(dist_host)
+    ld = _ld(dist_host) if dist_host is not None else 0
+    cap = int(lcs_host.numel()) if lcs_host is not None else 0
+    _check(ctx, load().lcs_solve_host(ctx, _ptr(a_host), int(a_host.numel()), _ptr(b_host), int(b_host.numel()),
+                                      dtype, _ptr(dist_host), ld, _ptr(lcs_host), cap, ctypes.byref(out),
+                                      _stream(stream)))
+    return out.value
+
+
+class Context:
+    """Owns one lcs_ctx (one per host thread)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.handle = lcs_create(device, mem_budget_bytes)
+
+    def close(self):
+        if self.handle is not None:
+            lcs_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,754 @@
+// lcs_api.cu -- the C ABI (include/lcs.h): context, tree planner, executor.
+//
+// Planner.  Rows of a are cut into S = ceil(m / h) strips.  Strips are merged
+// pairwise, level by level (an odd node at the end of a level is carried up
+// unchanged), into one root: the binary tree of Sec. II-A's recursive split,
+// with the strip builder standing in for the bottom log2(h) levels.  Every
+// node is stored in the narrowest integer type that holds the values of the
+// merge that reads it (DIST of a node is at most its row count), and in the
+// orientation that merge reads it in (upper operand by rows, lower operand by
+// columns).  All merges of one level run in one launch of each kernel.
+//
+// Executor.  strips -> per level: coarse K grid, tile refinement -> (root
+// merge into the caller's dense matrix if DIST is wanted) -> traceback: root
+// path, per level leftmost argmax top down, leaves, compaction.  Every node
+// of the tree stays resident until the traceback has passed it; the context
+// workspace is sized from the plan and never exceeds the budget.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lcs.h"
+#include "lcs_common.cuh"
+#include "lcs_kernels.h"
+
+using namespace lcsg;
+
+namespace {
+
+int dt_size(int dt) { return dt == DT_U8 ? 1 : (dt == DT_I16 ? 2 : 4); }
+int dt_for(int64_t maxval) { return maxval <= 255 ? DT_U8 : (maxval <= 32767 ? DT_I16 : DT_I32); }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int words_for(int h) {
+    const int w = (h + 31) / 32;
+    return w <= 1 ? 1 : (w <= 2 ? 2 : (w <= 4 ? 4 : 8));
+}
+
+int tile_cap(int in_dt) { return in_dt == DT_U8 ? 8 : (in_dt == DT_I16 ? 4 : 2); }
+
+struct Node {
+    int64_t row0 = 0, rows = 0;
+    int level = 0;
+    int dtype = DT_U8;
+    int layout = LAYOUT_ROW;
+    int parent = -1;
+    bool root = false;
+    size_t off = 0;        // storage offset in the workspace (non-root nodes)
+};
+
+struct Merge {
+    int u = -1, l = -1, out = -1;
+    int level = 0;
+    int in_dt = DT_U8, out_dt = DT_U8;
+    size_t kgrid_off = 0;
+};
+
+struct Group {               // merges of one level launched together
+    int level, in_dt, out_dt;
+    int begin, count;        // range in the job array
+    bool root;
+};
+
+struct Plan {
+    int64_t m = -1, n = -1;
+    int h = 0, words = 1, S = 0, levels = 0, root = -1;
+    int64_t NT = 0, P = 0;
+    int root_dt = DT_I32;    // dtype the root merge writes (caller's)
+    std::vector<Node> nodes;
+    std::vector<Merge> merges;         // in job order
+    std::vector<Group> groups;         // bottom-up
+    std::vector<std::pair<int, int>> tb_levels;   // top-down ranges in the tb array
+    // device arrays (offsets in the workspace)
+    size_t off_strip_outs = 0, off_jobs = 0, off_tb = 0, off_path = 0, off_counts = 0;
+    size_t off_slots = 0, off_vbuf = 0, total = 0;
+    std::vector<StripOut> h_strip_outs;
+    std::vector<MergeJob> h_jobs;
+    std::vector<TbMerge> h_tb;
+};
+
+constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int64) at 8
+
+}  // namespace
+
+struct lcs_ctx {
+    int device = 0;
+    size_t budget = 0;
+    int32_t strip_h = 0;
+    char *ws = nullptr;          // plan workspace
+    size_t ws_bytes = 0;
+    char *io = nullptr;          // host-call staging (lcs_solve_host, lcs_merge)
+    size_t io_bytes = 0;
+    size_t peak = 0;
+    std::string last_error;
+    lcs_stats stats{};
+    Plan plan;
+    bool plan_uploaded = false;
+    int launches = 0;
+};
+
+namespace {
+
+lcs_status fail(lcs_ctx *ctx, lcs_status s, const std::string &what) {
+    if (ctx) ctx->last_error = what;
+    return s;
+}
+
+lcs_status cuda_fail(lcs_ctx *ctx, cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, LCS_ENOMEM, msg);
+    return fail(ctx, LCS_ECUDA, msg);
+}
+
+#define LCS_CK(ctx, expr)                                      \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+#define LCS_LAUNCH(ctx, expr)                                  \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+        (ctx)->launches++;                                     \
+    } while (0)
+
+int auto_strip_height(int64_t m, int64_t n) {
+    (void)n;
+    if (m <= 128) return (int)std::max<int64_t>(m, 1);
+    return 128;
+}
+
+Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
+    Plan P;
+    P.m = m; P.n = n; P.h = h; P.words = words_for(h); P.root_dt = root_dt;
+    P.S = (int)ceil_div(m, h);
+    P.NT = num_tiles_side(n);
+    P.P = ceil_div(n, T);
+    for (int s = 0; s < P.S; ++s) {
+        Node nd;
+        nd.row0 = (int64_t)s * h;
+        nd.rows = std::min<int64_t>(h, m - nd.row0);
+        P.nodes.push_back(nd);
+    }
+    std::vector<int> cur(P.S);
+    for (int s = 0; s < P.S; ++s) cur[s] = s;
+    int level = 0;
+    std::vector<Merge> merges;
+    while (cur.size() > 1) {
+        ++level;
+        std::vector<int> next;
+        for (size_t q = 0; q < cur.size(); q += 2) {
+            if (q + 1 < cur.size()) {
+                Node nd;
+                nd.row0 = P.nodes[cur[q]].row0;
+                nd.rows = P.nodes[cur[q]].rows + P.nodes[cur[q + 1]].rows;
+                nd.level = level;
+                P.nodes.push_back(nd);
+                const int out = (int)P.nodes.size() - 1;
+                Merge mg;
+                mg.u = cur[q]; mg.l = cur[q + 1]; mg.out = out; mg.level = level;
+                P.nodes[mg.u].parent = out; P.nodes[mg.u].layout = LAYOUT_ROW;
+                P.nodes[mg.l].parent = out; P.nodes[mg.l].layout = LAYOUT_COL;
+                merges.push_back(mg);
+                next.push_back(out);
+            } else {
+                next.push_back(cur[q]);
+            }
+        }
+        cur.swap(next);
+    }
+    P.levels = level;
+    P.root = cur[0];
+    P.nodes[P.root].root = true;
+    for (auto &mg : merges) {
+        mg.in_dt = dt_for(std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows));
+        P.nodes[mg.u].dtype = mg.in_dt;
+        P.nodes[mg.l].dtype = mg.in_dt;
+    }
+    for (auto &mg : merges) mg.out_dt = (mg.out == P.root) ? root_dt : P.nodes[mg.out].dtype;
+    // Strips need a dtype even when S == 1 (unused then).
+    // Job order: level ascending, then (in_dt, out_dt), the root merge last.
+    std::stable_sort(merges.begin(), merges.end(), [&](const Merge &x, const Merge &y) {
+        const bool rx = x.out == P.root, ry = y.out == P.root;
+        if (x.level != y.level) return x.level < y.level;
+        if (rx != ry) return ry;
+        if (x.in_dt != y.in_dt) return x.in_dt < y.in_dt;
+        return x.out_dt < y.out_dt;
+    });
+    P.merges = merges;
+
+    // Workspace layout.
+    size_t off = kHeaderBytes;
+    const int64_t tiles = num_tiles_tri(P.NT);
+    for (size_t v = 0; v < P.nodes.size(); ++v) {
+        Node &nd = P.nodes[v];
+        if (nd.root) continue;
+        nd.off = off;
+        off = align256(off + (size_t)tiles * T2 * dt_size(nd.dtype));
+    }
+    for (auto &mg : P.merges) {
+        mg.kgrid_off = off;
+        off = align256(off + (size_t)(P.P + 1) * (P.P + 1) * 4);
+    }
+    P.off_strip_outs = off; off = align256(off + sizeof(StripOut) * P.S);
+    P.off_jobs = off; off = align256(off + sizeof(MergeJob) * std::max<size_t>(1, P.merges.size()));
+    P.off_tb = off; off = align256(off + sizeof(TbMerge) * std::max<size_t>(1, P.merges.size()));
+    P.off_path = off; off = align256(off + sizeof(int32_t) * 2 * P.nodes.size());
+    P.off_counts = off; off = align256(off + sizeof(int32_t) * 2 * P.S);
+    P.off_slots = off; off = align256(off + (size_t)P.S * h);
+    P.off_vbuf = off; off = align256(off + (size_t)(n + P.S + 1) * P.words * 4);
+    P.total = off;
+
+    // Groups (bottom-up) and traceback ranges (top-down).
+    for (int q = 0; q < (int)P.merges.size();) {
+        const Merge &a = P.merges[q];
+        int e = q + 1;
+        while (e < (int)P.merges.size()) {
+            const Merge &b = P.merges[e];
+            if (b.level != a.level || b.in_dt != a.in_dt || b.out_dt != a.out_dt ||
+                (b.out == P.root) != (a.out == P.root))
+                break;
+            ++e;
+        }
+        P.groups.push_back(Group{a.level, a.in_dt, a.out_dt, q, e - q, a.out == P.root});
+        q = e;
+    }
+    // tb array: level descending.
+    std::vector<int> order(P.merges.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return P.merges[x].level > P.merges[y].level; });
+    for (size_t q = 0; q < order.size();) {
+        size_t e = q + 1;
+        while (e < order.size() && P.merges[order[e]].level == P.merges[order[q]].level) ++e;
+        P.tb_levels.push_back({(int)q, (int)(e - q)});
+        q = e;
+    }
+    P.h_tb.resize(order.size());
+    for (size_t q = 0; q < order.size(); ++q) {
+        const Merge &mg = P.merges[order[q]];
+        TbMerge t{};
+        t.U = reinterpret_cast<const void *>(P.nodes[mg.u].off);   // relocated at upload
+        t.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
+        t.in_dtype = mg.in_dt;
+        t.node = mg.out; t.upper = mg.u; t.lower = mg.l;
+        P.h_tb[q] = t;
+    }
+    P.h_jobs.resize(P.merges.size());
+    for (size_t q = 0; q < P.merges.size(); ++q) {
+        const Merge &mg = P.merges[q];
+        MergeJob j{};
+        j.U = reinterpret_cast<const void *>(P.nodes[mg.u].off);
+        j.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
+        j.D = (mg.out == P.root) ? nullptr : reinterpret_cast<void *>(P.nodes[mg.out].off);
+        j.kgrid = reinterpret_cast<int32_t *>(mg.kgrid_off);
+        j.d_layout = (mg.out == P.root) ? LAYOUT_DENSE : P.nodes[mg.out].layout;
+        P.h_jobs[q] = j;
+    }
+    P.h_strip_outs.resize(P.S);
+    for (int s = 0; s < P.S; ++s) {
+        StripOut o{};
+        o.base = reinterpret_cast<void *>(P.nodes[s].off);
+        o.layout = P.nodes[s].layout;
+        P.h_strip_outs[s] = o;
+    }
+    return P;
+}
+
+template <typename X> X *reloc(char *base, X *off) {
+    return reinterpret_cast<X *>(base + reinterpret_cast<uintptr_t>(off));
+}
+
+lcs_status ensure_workspace(lcs_ctx *ctx, size_t bytes) {
+    if (bytes + ctx->io_bytes > ctx->budget)
+        return fail(ctx, LCS_ENOMEM, "workspace of " + std::to_string(bytes) + " bytes exceeds the budget");
+    if (ctx->ws_bytes >= bytes) return LCS_OK;
+    if (ctx->ws) {
+        LCS_CK(ctx, cudaDeviceSynchronize());
+        LCS_CK(ctx, cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    LCS_CK(ctx, cudaMalloc(&ctx->ws, bytes));
+    LCS_CK(ctx, cudaMemset(ctx->ws, 0, kHeaderBytes));
+    ctx->ws_bytes = bytes;
+    ctx->peak = std::max(ctx->peak, ctx->ws_bytes + ctx->io_bytes);
+    ctx->plan_uploaded = false;
+    return LCS_OK;
+}
+
+lcs_status ensure_io(lcs_ctx *ctx, size_t bytes) {
+    if (ctx->io_bytes >= bytes) return LCS_OK;
+    if (bytes + ctx->ws_bytes > ctx->budget)
+        return fail(ctx, LCS_ENOMEM, "staging of " + std::to_string(bytes) + " bytes exceeds the budget");
+    if (ctx->io) {
+        LCS_CK(ctx, cudaDeviceSynchronize());
+        LCS_CK(ctx, cudaFree(ctx->io));
+        ctx->io = nullptr;
+        ctx->io_bytes = 0;
+    }
+    LCS_CK(ctx, cudaMalloc(&ctx->io, bytes));
+    ctx->io_bytes = bytes;
+    ctx->peak = std::max(ctx->peak, ctx->ws_bytes + ctx->io_bytes);
+    return LCS_OK;
+}
+
+// Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
+lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
+    const int h = ctx->strip_h > 0 ? ctx->strip_h : auto_strip_height(m, n);
+    Plan &P = ctx->plan;
+    if (!(P.m == m && P.n == n && P.h == h && P.root_dt == root_dt)) {
+        // Kernels of an earlier call may still read the old descriptors.
+        LCS_CK(ctx, cudaDeviceSynchronize());
+        ctx->plan = build_plan(m, n, h, root_dt);
+        ctx->plan_uploaded = false;
+    }
+    lcs_status s = ensure_workspace(ctx, ctx->plan.total);
+    if (s != LCS_OK) return s;
+    if (!ctx->plan_uploaded) {
+        Plan &Q = ctx->plan;
+        char *base = ctx->ws;
+        std::vector<StripOut> so = Q.h_strip_outs;
+        for (auto &o : so) o.base = reloc(base, (char *)o.base);
+        std::vector<MergeJob> jobs = Q.h_jobs;
+        for (auto &j : jobs) {
+            j.U = reloc(base, (const char *)j.U);
+            j.L = reloc(base, (const char *)j.L);
+            if (j.D) j.D = reloc(base, (char *)j.D);
+            j.kgrid = reloc(base, j.kgrid);
+        }
+        std::vector<TbMerge> tb = Q.h_tb;
+        for (auto &t : tb) {
+            t.U = reloc(base, (const char *)t.U);
+            t.L = reloc(base, (const char *)t.L);
+        }
+        LCS_CK(ctx, cudaMemcpy(base + Q.off_strip_outs, so.data(), sizeof(StripOut) * so.size(),
+                               cudaMemcpyHostToDevice));
+        if (!jobs.empty()) {
+            LCS_CK(ctx, cudaMemcpy(base + Q.off_jobs, jobs.data(), sizeof(MergeJob) * jobs.size(),
+                                   cudaMemcpyHostToDevice));
+            LCS_CK(ctx, cudaMemcpy(base + Q.off_tb, tb.data(), sizeof(TbMerge) * tb.size(),
+                                   cudaMemcpyHostToDevice));
+        }
+        ctx->plan_uploaded = true;
+    }
+    return LCS_OK;
+}
+
+int *err_word(lcs_ctx *ctx) { return reinterpret_cast<int *>(ctx->ws); }
+int64_t *len_word(lcs_ctx *ctx) { return reinterpret_cast<int64_t *>(ctx->ws + 8); }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+lcs_status check_dense(lcs_ctx *ctx, const void *p, int64_t n, int64_t ld, int dt, const char *name) {
+    if (!p) return fail(ctx, LCS_EINVAL, std::string(name) + " is NULL");
+    if (ld < n + 1) return fail(ctx, LCS_EINVAL, std::string(name) + ": ld < n+1");
+    if ((ld * dt_size(dt)) % 16 != 0) return fail(ctx, LCS_EINVAL, std::string(name) + ": ld*size % 16 != 0");
+    if (!aligned16(p)) return fail(ctx, LCS_EINVAL, std::string(name) + " is not 16-byte aligned");
+    return LCS_OK;
+}
+
+int api_dt(lcs_dtype d) { return d == LCS_I16 ? DT_I16 : DT_I32; }
+
+// The whole hot path on device buffers (see lcs_solve in lcs.h).
+lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                        lcs_dtype dtype, void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap,
+                        int32_t *cross, int64_t *len_dev_out, bool need_len, cudaStream_t st) {
+    ctx->launches = 0;
+    const int rdt = api_dt(dtype);
+    if (m < 0 || n < 0) return fail(ctx, LCS_EINVAL, "negative length");
+    if (n >= INT32_MAX / 2 || m >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "length too large");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    if (dtype == LCS_I16 && (m >= 32768 || n >= 32768)) return fail(ctx, LCS_EINVAL, "LCS_I16 needs m, n < 32768");
+    if (dist) {
+        lcs_status s = check_dense(ctx, dist, n, ld, rdt, "dist");
+        if (s != LCS_OK) return s;
+    }
+    if (out_lcs && cap < std::min(m, n)) return fail(ctx, LCS_EOVERFLOW, "cap < min(m, n)");
+    if ((m > 0 && !a) || (n > 0 && !b)) return fail(ctx, LCS_EINVAL, "a or b is NULL");
+    const bool want_tb = out_lcs || cross;
+    const bool want_len = need_len || len_dev_out;
+
+    // Degenerate grids: no rows or no columns.
+    if (m == 0 || n == 0) {
+        lcs_status s = ensure_workspace(ctx, std::max(ctx->ws_bytes, kHeaderBytes));
+        if (s != LCS_OK) return s;
+        if (dist) {
+            LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 1,
+                                              nullptr, st));
+        }
+        LCS_CK(ctx, cudaMemsetAsync(len_word(ctx), 0, sizeof(int64_t), st));
+        if (len_dev_out) LCS_CK(ctx, cudaMemsetAsync(len_dev_out, 0, sizeof(int64_t), st));
+        if (cross) {
+            // v[r] = 0 for every row when n == 0; with m == 0 there is only v[0] = 0.
+            LCS_CK(ctx, cudaMemsetAsync(cross, 0, sizeof(int32_t) * (m + 1), st));
+        }
+        ctx->stats.strips = 0; ctx->stats.merges = 0; ctx->stats.tree_levels = 0;
+        ctx->stats.kernel_launches = ctx->launches;
+        return LCS_OK;
+    }
+
+    lcs_status s = prepare(ctx, m, n, rdt);
+    if (s != LCS_OK) return s;
+    Plan &P = ctx->plan;
+    char *base = ctx->ws;
+    int *err = err_word(ctx);
+    int32_t *pathI = reinterpret_cast<int32_t *>(base + P.off_path);
+    int32_t *pathJ = pathI + P.nodes.size();
+    int32_t *counts = reinterpret_cast<int32_t *>(base + P.off_counts);
+    uint8_t *slots = reinterpret_cast<uint8_t *>(base + P.off_slots);
+
+    // 1. strips
+    if (P.S == 1) {
+        if (dist) {
+            StripParams sp{};
+            sp.a = a; sp.m = m; sp.h = P.h; sp.S = 1; sp.b = b; sp.n = n; sp.NT = P.NT;
+            sp.outs = nullptr; sp.dense = dist; sp.ld = ld; sp.band_first = 0;
+            LCS_LAUNCH(ctx, launch_strip(sp, rdt, P.words, st));
+            if (P.NT > 1)
+                LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                                                  nullptr, st));
+        }
+    } else {
+        // All strips share one dtype here (heights <= h, h <= 256 -> u8/i16).
+        StripParams sp{};
+        sp.a = a; sp.m = m; sp.h = P.h; sp.S = P.S; sp.b = b; sp.n = n; sp.NT = P.NT;
+        sp.outs = reinterpret_cast<const StripOut *>(base + P.off_strip_outs);
+        sp.dense = nullptr; sp.ld = 0; sp.band_first = 0;
+        // Strips feeding merges of different input types: launch per dtype.
+        int dts[3] = {DT_U8, DT_I16, DT_I32};
+        for (int dt : dts) {
+            bool any = false, all = true;
+            for (int q = 0; q < P.S; ++q) {
+                if (P.nodes[q].dtype == dt) any = true; else all = false;
+            }
+            if (!any) continue;
+            if (all) {
+                LCS_LAUNCH(ctx, launch_strip(sp, dt, P.words, st));
+            } else {
+                for (int q = 0; q < P.S; ++q) {
+                    if (P.nodes[q].dtype != dt) continue;
+                    StripParams one = sp;
+                    one.a = a + (int64_t)q * P.h;
+                    one.m = P.nodes[q].rows;
+                    one.S = 1;
+                    one.outs = sp.outs + q;
+                    LCS_LAUNCH(ctx, launch_strip(one, dt, P.words, st));
+                }
+            }
+        }
+        // 2. merges, level by level
+        const int64_t sigma0 = coarse_sigma0(P.P);
+        for (const Group &g : P.groups) {
+            if (g.root && !dist) continue;
+            MergeParams mp{};
+            mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
+            mp.njobs = g.count;
+            mp.cap = tile_cap(g.in_dt);
+            mp.n = n; mp.NT = P.NT; mp.P = P.P; mp.ld = ld; mp.err = err;
+            mp.dense_out = g.root ? dist : nullptr;
+            mp.dense_K = nullptr;
+            mp.sigma = (int32_t)sigma0; mp.full = 1;
+            LCS_LAUNCH(ctx, launch_coarse(mp, g.in_dt, st));
+            for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
+                mp.sigma = (int32_t)sg; mp.full = 0;
+                LCS_LAUNCH(ctx, launch_coarse(mp, g.in_dt, st));
+            }
+            LCS_LAUNCH(ctx, launch_tile(mp, g.in_dt, g.out_dt, st));
+            if (g.root)
+                LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                                                  nullptr, st));
+        }
+    }
+
+    // 3. traceback / length
+    if (want_tb || (want_len && P.S == 1)) {
+        LCS_LAUNCH(ctx, launch_root_path(pathI, pathJ, P.root, n, st));
+        const TbMerge *tbd = reinterpret_cast<const TbMerge *>(base + P.off_tb);
+        for (auto &lv : P.tb_levels) {
+            TbParams tp{};
+            tp.merges = tbd + lv.first; tp.count = lv.second;
+            tp.n = n; tp.NT = P.NT; tp.pathI = pathI; tp.pathJ = pathJ;
+            tp.len_out = nullptr; tp.root_node = P.root; tp.err = err;
+            LCS_LAUNCH(ctx, launch_tb_level(tp, st));
+        }
+        LeafParams lp{};
+        lp.a = a; lp.m = m; lp.h = P.h; lp.S = P.S; lp.b = b; lp.n = n;
+        lp.pathI = pathI; lp.pathJ = pathJ;
+        lp.vbuf = reinterpret_cast<uint32_t *>(base + P.off_vbuf);
+        lp.words = P.words; lp.slots = slots; lp.counts = counts; lp.cross = cross; lp.err = err;
+        LCS_LAUNCH(ctx, launch_leaf(lp, st));
+        CompactParams cp{};
+        cp.slots = slots; cp.counts = counts; cp.S = P.S; cp.h = P.h;
+        cp.out = out_lcs; cp.cap = cap; cp.len_out = len_word(ctx); cp.len_out2 = len_dev_out; cp.err = err;
+        LCS_LAUNCH(ctx, launch_compact(cp, st));
+    } else if (want_len) {
+        // Root maximum only: the first traceback level.
+        LCS_LAUNCH(ctx, launch_root_path(pathI, pathJ, P.root, n, st));
+        const TbMerge *tbd = reinterpret_cast<const TbMerge *>(base + P.off_tb);
+        TbParams tp{};
+        tp.merges = tbd + P.tb_levels[0].first; tp.count = P.tb_levels[0].second;
+        tp.n = n; tp.NT = P.NT; tp.pathI = pathI; tp.pathJ = pathJ;
+        tp.len_out = len_word(ctx); tp.root_node = P.root; tp.err = err;
+        LCS_LAUNCH(ctx, launch_tb_level(tp, st));
+        if (len_dev_out) LCS_CK(ctx, launch_copy_len(len_word(ctx), len_dev_out, st));
+    }
+    ctx->stats.strip_height = P.h;
+    ctx->stats.strips = P.S;
+    ctx->stats.merges = (int32_t)P.merges.size();
+    ctx->stats.tree_levels = P.levels;
+    ctx->stats.kernel_launches = ctx->launches;
+    ctx->stats.tile = T;
+    return LCS_OK;
+}
+
+// Synchronise and read the error and length words (one 16-byte copy).
+lcs_status read_back(lcs_ctx *ctx, cudaStream_t st, int64_t *len_host) {
+    int64_t hdr[2] = {0, 0};
+    LCS_CK(ctx, cudaMemcpyAsync(hdr, ctx->ws, 16, cudaMemcpyDeviceToHost, st));
+    LCS_CK(ctx, cudaStreamSynchronize(st));
+    const int errbits = (int)(hdr[0] & 0xFFFFFFFF);
+    if (errbits) {
+        LCS_CK(ctx, cudaMemset(ctx->ws, 0, 4));
+        if (errbits & ERR_TIMEOUT) return fail(ctx, LCS_ETIMEOUT, "a device-side wait timed out");
+        if (errbits & ERR_OVERFLOW) return fail(ctx, LCS_EOVERFLOW, "a value or the output exceeded its capacity");
+        return fail(ctx, LCS_ECUDA, "device-side consistency check failed");
+    }
+    if (len_host) *len_host = hdr[1];
+    return LCS_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+lcs_status lcs_create(lcs_ctx **out, int device, size_t mem_budget_bytes) {
+    if (!out) return LCS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return LCS_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return LCS_ECUDA;
+    lcs_ctx *ctx = new (std::nothrow) lcs_ctx();
+    if (!ctx) return LCS_ENOMEM;
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)64 << 30;
+    *out = ctx;
+    return LCS_OK;
+}
+
+lcs_status lcs_destroy(lcs_ctx *ctx) {
+    if (!ctx) return LCS_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->io) cudaFree(ctx->io);
+    delete ctx;
+    return LCS_OK;
+}
+
+const char *lcs_strerror(lcs_status s) {
+    switch (s) {
+        case LCS_OK: return "ok";
+        case LCS_EINVAL: return "invalid argument";
+        case LCS_ENOMEM: return "out of memory (workspace budget or device)";
+        case LCS_ETIMEOUT: return "device-side wait timed out";
+        case LCS_ECUDA: return "CUDA error";
+        case LCS_EAGAIN: return "try again";
+        case LCS_EOVERFLOW: return "value or output exceeds its capacity";
+    }
+    return "unknown status";
+}
+
+const char *lcs_last_error(lcs_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
+    if (!ctx || h < 0 || h > 256) return fail(ctx, LCS_EINVAL, "strip height must be 0..256");
+    ctx->strip_h = h;
+    return LCS_OK;
+}
+
+lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out) {
+    if (!ctx || !out) return LCS_EINVAL;
+    ctx->stats.workspace_bytes = (int64_t)(ctx->ws_bytes + ctx->io_bytes);
+    ctx->stats.peak_workspace_bytes = (int64_t)ctx->peak;
+    *out = ctx->stats;
+    return LCS_OK;
+}
+
+lcs_status lcs_sync(lcs_ctx *ctx, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->ws) {
+        LCS_CK(ctx, cudaStreamSynchronize(st));
+        return LCS_OK;
+    }
+    return read_back(ctx, st, nullptr);
+}
+
+lcs_status lcs_strip_dist(lcs_ctx *ctx, const uint8_t *a_strip, int32_t h, const uint8_t *b, int64_t n,
+                          lcs_dtype dtype, void *dist, int64_t ld, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    ctx->launches = 0;
+    if (h < 1 || h > 256) return fail(ctx, LCS_EINVAL, "h must be 1..256");
+    if (n < 0 || n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "n out of range");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    if (dtype == LCS_I16 && n >= 32768) return fail(ctx, LCS_EINVAL, "LCS_I16 needs n < 32768");
+    if (!a_strip || (n > 0 && !b)) return fail(ctx, LCS_EINVAL, "a_strip or b is NULL");
+    const int rdt = api_dt(dtype);
+    lcs_status s = check_dense(ctx, dist, n, ld, rdt, "dist");
+    if (s != LCS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    StripParams sp{};
+    sp.a = a_strip; sp.m = h; sp.h = h; sp.S = 1; sp.b = b; sp.n = n; sp.NT = num_tiles_side(n);
+    sp.outs = nullptr; sp.dense = dist; sp.ld = ld; sp.band_first = 0;
+    LCS_LAUNCH(ctx, launch_strip(sp, rdt, words_for(h), st));
+    if (sp.NT > 1)
+        LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, nullptr, st));
+    ctx->stats.kernel_launches = ctx->launches;
+    return LCS_OK;
+}
+
+lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64_t n, lcs_dtype dtype,
+                     int64_t ld, void *dist_out, int32_t *argmax_out, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    ctx->launches = 0;
+    if (n < 0 || n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "n out of range");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    const int dt = api_dt(dtype);
+    lcs_status s;
+    if ((s = check_dense(ctx, dist_u, n, ld, dt, "dist_u")) != LCS_OK) return s;
+    if ((s = check_dense(ctx, dist_l, n, ld, dt, "dist_l")) != LCS_OK) return s;
+    if ((s = check_dense(ctx, dist_out, n, ld, dt, "dist_out")) != LCS_OK) return s;
+    if (argmax_out && !aligned16(argmax_out)) return fail(ctx, LCS_EINVAL, "argmax_out is not 16-byte aligned");
+    if (dist_out == dist_u || dist_out == dist_l) return fail(ctx, LCS_EINVAL, "dist_out aliases an input");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t NT = num_tiles_side(n), P = ceil_div(n, T);
+    const size_t packed = align256((size_t)num_tiles_tri(NT) * T2 * dt_size(dt));
+    const size_t kg = align256((size_t)(P + 1) * (P + 1) * 4);
+    const size_t need = kHeaderBytes + 2 * packed + kg + align256(sizeof(MergeJob));
+    if ((s = ensure_workspace(ctx, std::max(ctx->ws_bytes, kHeaderBytes))) != LCS_OK) return s;
+    if ((s = ensure_io(ctx, need)) != LCS_OK) return s;
+    char *io = ctx->io;
+    char *Up = io + kHeaderBytes, *Lp = Up + packed;
+    int32_t *kgrid = reinterpret_cast<int32_t *>(Lp + packed);
+    MergeJob *jobd = reinterpret_cast<MergeJob *>(Lp + packed + kg);
+    LCS_LAUNCH(ctx, launch_pack(dist_u, dt, n, ld, Up, LAYOUT_ROW, st));
+    LCS_LAUNCH(ctx, launch_pack(dist_l, dt, n, ld, Lp, LAYOUT_COL, st));
+    MergeJob job{};
+    job.U = Up; job.L = Lp; job.D = nullptr; job.kgrid = kgrid; job.d_layout = LAYOUT_DENSE;
+    LCS_CK(ctx, cudaMemcpyAsync(jobd, &job, sizeof(job), cudaMemcpyHostToDevice, st));
+    MergeParams mp{};
+    mp.jobs = jobd; mp.njobs = 1; mp.cap = tile_cap(dt);
+    mp.n = n; mp.NT = NT; mp.P = P; mp.ld = ld; mp.err = err_word(ctx);
+    mp.dense_out = dist_out; mp.dense_K = argmax_out;
+    const int64_t sigma0 = coarse_sigma0(std::max<int64_t>(P, 1));
+    mp.sigma = (int32_t)sigma0; mp.full = 1;
+    LCS_LAUNCH(ctx, launch_coarse(mp, dt, st));
+    for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
+        mp.sigma = (int32_t)sg; mp.full = 0;
+        LCS_LAUNCH(ctx, launch_coarse(mp, dt, st));
+    }
+    LCS_LAUNCH(ctx, launch_tile(mp, dt, dt, st));
+    LCS_LAUNCH(ctx, launch_fill_dense(dist_out, dt, n, ld, dt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, argmax_out, st));
+    // The job descriptor lives on the host stack: make sure the copy is done.
+    LCS_CK(ctx, cudaStreamSynchronize(st));
+    ctx->stats.kernel_launches = ctx->launches;
+    return LCS_OK;
+}
+
+lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, lcs_dtype dtype,
+                     void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap, int32_t *cross,
+                     int64_t *out_len_device, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    return solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, cross, out_len_device, false,
+                        (cudaStream_t)stream);
+}
+
+lcs_status lcs_dist(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, lcs_dtype dtype,
+                    void *dist, int64_t ld, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    if (!dist) return fail(ctx, LCS_EINVAL, "dist is NULL");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    return solve_device(ctx, a, m, b, n, dtype, dist, ld, nullptr, 0, nullptr, nullptr, false,
+                        (cudaStream_t)stream);
+}
+
+lcs_status lcs_length(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                      int64_t *out_len_host, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    if (!out_len_host) return fail(ctx, LCS_EINVAL, "out_len_host is NULL");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    lcs_status s = solve_device(ctx, a, m, b, n, LCS_I32, nullptr, 0, nullptr, 0, nullptr, nullptr, true, st);
+    if (s != LCS_OK) return s;
+    return read_back(ctx, st, out_len_host);
+}
+
+lcs_status lcs_traceback(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                         uint8_t *out_lcs, int64_t cap, int64_t *out_len_host, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    if (!out_lcs || !out_len_host) return fail(ctx, LCS_EINVAL, "out_lcs or out_len_host is NULL");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    lcs_status s = solve_device(ctx, a, m, b, n, LCS_I32, nullptr, 0, out_lcs, cap, nullptr, nullptr, true, st);
+    if (s != LCS_OK) return s;
+    return read_back(ctx, st, out_len_host);
+}
+
+lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const uint8_t *b_host, int64_t n,
+                          lcs_dtype dtype, void *dist_host, int64_t ld, uint8_t *lcs_host, int64_t cap,
+                          int64_t *out_len_host, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    if (!out_len_host) return fail(ctx, LCS_EINVAL, "out_len_host is NULL");
+    if (m < 0 || n < 0) return fail(ctx, LCS_EINVAL, "negative length");
+    if ((m > 0 && !a_host) || (n > 0 && !b_host)) return fail(ctx, LCS_EINVAL, "a_host or b_host is NULL");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    if (dist_host && ld < n + 1) return fail(ctx, LCS_EINVAL, "ld < n+1");
+    if (lcs_host && cap < std::min(m, n)) return fail(ctx, LCS_EOVERFLOW, "cap < min(m, n)");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rdt = api_dt(dtype);
+    const int64_t ldd = dist_host ? ((n + 1) * dt_size(rdt) + 15) / 16 * 16 / dt_size(rdt) : 0;
+    const size_t dist_bytes = dist_host ? align256((size_t)(n + 1) * ldd * dt_size(rdt)) : 0;
+    const size_t a_off = 0, b_off = align256((size_t)m), l_off = b_off + align256((size_t)n);
+    const size_t d_off = l_off + align256((size_t)std::max<int64_t>(cap, 1));
+    lcs_status s = ensure_io(ctx, d_off + dist_bytes + 256);
+    if (s != LCS_OK) return s;
+    char *io = ctx->io;
+    if (m) LCS_CK(ctx, cudaMemcpyAsync(io + a_off, a_host, m, cudaMemcpyHostToDevice, st));
+    if (n) LCS_CK(ctx, cudaMemcpyAsync(io + b_off, b_host, n, cudaMemcpyHostToDevice, st));
+    void *dd = dist_host ? (void *)(io + d_off) : nullptr;
+    uint8_t *ld_lcs = lcs_host ? reinterpret_cast<uint8_t *>(io + l_off) : nullptr;
+    s = solve_device(ctx, reinterpret_cast<const uint8_t *>(io + a_off), m, reinterpret_cast<const uint8_t *>(io + b_off),
+                     n, dtype, dd, ldd, ld_lcs, cap, nullptr, nullptr, true, st);
+    if (s != LCS_OK) return s;
+    int64_t len = 0;
+    s = read_back(ctx, st, &len);
+    if (s != LCS_OK) return s;
+    if (dist_host) {
+        LCS_CK(ctx, cudaMemcpy2DAsync(dist_host, (size_t)ld * dt_size(rdt), dd, (size_t)ldd * dt_size(rdt),
+                                      (size_t)(n + 1) * dt_size(rdt), (size_t)(n + 1), cudaMemcpyDeviceToHost, st));
+    }
+    if (lcs_host && len > 0) LCS_CK(ctx, cudaMemcpyAsync(lcs_host, ld_lcs, (size_t)len, cudaMemcpyDeviceToHost, st));
+    LCS_CK(ctx, cudaStreamSynchronize(st));
+    *out_len_host = len;
+    return LCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// lcs_common.cuh -- layout, types and PTX helpers shared by the GB300 kernels.
+//
+// Internal DIST storage ("tile-packed").  A DIST matrix over vertices 0..n is
+// cut into T x T tiles (T = 64); only tiles (I, J) with I <= J exist.  A node
+// that the merge above it reads by ROWS (the upper operand U) is stored in
+// row layout: tiles ordered by I then J, each tile row-major (i-major).  A
+// node read by COLUMNS (the lower operand L) is stored in column layout:
+// tiles ordered by J then I, each tile j-major (the tile is stored
+// transposed).  In both layouts the band of tiles a merge tile needs --
+// U(i in tile I, k in K-tiles) or L(k in K-tiles, j in tile J) -- is one
+// contiguous run of whole tiles, so it is staged into shared memory with one
+// TMA bulk copy per tile, and every scan over k reads consecutive addresses.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lcsg {
+
+constexpr int T = 64;          // tile edge in vertices
+constexpr int T_SHIFT = 6;
+constexpr int T2 = T * T;
+
+enum DType : int { DT_I32 = 0, DT_I16 = 1, DT_U8 = 2 };
+enum Layout : int { LAYOUT_ROW = 0, LAYOUT_COL = 1, LAYOUT_DENSE = 2 };
+
+// Device error word bits (read back by lcs_sync).
+enum ErrBits : int { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_BOUNDS = 4 };
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t num_tiles_side(int64_t n) { return ceil_div(n + 1, T); }
+__host__ __device__ inline int64_t num_tiles_tri(int64_t NT) { return NT * (NT + 1) / 2; }
+// Row layout: tile (I, J >= I) -> I*NT - I*(I-1)/2 + (J - I).
+__host__ __device__ inline int64_t row_tile(int64_t I, int64_t J, int64_t NT) {
+    return I * NT - I * (I - 1) / 2 + (J - I);
+}
+// Column layout: tile (I <= J, J) -> J*(J+1)/2 + I.
+__host__ __device__ inline int64_t col_tile(int64_t I, int64_t J) { return J * (J + 1) / 2 + I; }
+
+// Element (i, k) of a row-layout matrix, k >= i.
+__device__ __forceinline__ int64_t row_elem(int64_t i, int64_t k, int64_t NT) {
+    return row_tile(i >> T_SHIFT, k >> T_SHIFT, NT) * T2 + ((i & (T - 1)) << T_SHIFT) + (k & (T - 1));
+}
+// Element (k, j) of a column-layout matrix, k <= j.
+__device__ __forceinline__ int64_t col_elem(int64_t k, int64_t j) {
+    return col_tile(k >> T_SHIFT, j >> T_SHIFT) * T2 + ((j & (T - 1)) << T_SHIFT) + (k & (T - 1));
+}
+
+template <typename V> struct Sentinel;
+template <> struct Sentinel<int32_t> { static constexpr int32_t value = INT32_MIN; };
+template <> struct Sentinel<int16_t> { static constexpr int16_t value = INT16_MIN; };
+template <> struct Sentinel<uint8_t> { static constexpr uint8_t value = 0xFF; };
+
+template <typename V> struct MaxVal;
+template <> struct MaxVal<int32_t> { static constexpr int value = INT32_MAX; };
+template <> struct MaxVal<int16_t> { static constexpr int value = INT16_MAX; };
+template <> struct MaxVal<uint8_t> { static constexpr int value = 255; };
+
+__device__ __forceinline__ int load_any(const void *p, int64_t idx, int dt) {
+    if (dt == DT_U8) return ((const uint8_t *)p)[idx];
+    if (dt == DT_I16) return ((const int16_t *)p)[idx];
+    return ((const int32_t *)p)[idx];
+}
+
+__device__ __forceinline__ void set_error(int *err, int bits) {
+    if (err) atomicOr(err, bits);
+}
+
+// ---------------------------------------------------------------- PTX: mbarrier + TMA bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One TMA bulk copy global -> shared, completing `bytes` transactions on bar.
+// dst and src must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~max_ns of global time
+// and returns false (the caller records ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint64_t max_ns) {
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (mbar_try_wait(bar, phase)) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > max_ns) return false;
+    }
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+}  // namespace lcsg

@@ -1,0 +1,135 @@
+// lcs_kernels.h -- host-side declarations of the kernel launchers and the
+// job descriptors they read from device memory.  Internal to the library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lcsg {
+
+// ------------------------------------------------------------- strip builder
+struct StripOut {
+    void *base;        // tile-packed storage of this strip's DIST
+    int32_t layout;    // LAYOUT_ROW or LAYOUT_COL
+    int32_t pad;
+};
+
+struct StripParams {
+    const uint8_t *a;      // first row of strip 0
+    int64_t m;             // rows in all strips together
+    int32_t h;             // rows per strip (the last strip may be shorter)
+    int32_t S;             // number of strips
+    const uint8_t *b;
+    int64_t n;
+    int64_t NT;            // tiles per side = ceil((n+1)/T)
+    const StripOut *outs;  // [S] packed outputs (device array), or
+    void *dense;           // dense (n+1) x ld output of strip 0 (S must be 1)
+    int64_t ld;
+    int32_t band_first;    // first band (tile row) this launch covers
+    int32_t pad;
+};
+
+// out_dtype: DT_*; words = 32-bit words per source (1, 2, 4 or 8).
+cudaError_t launch_strip(const StripParams &p, int out_dtype, int words, cudaStream_t st);
+
+// ------------------------------------------------------------- merge
+struct MergeJob {
+    const void *U;       // upper operand, row layout
+    const void *L;       // lower operand, column layout
+    void *D;             // output: packed (row/col layout) or dense (n+1) x ld
+    int32_t *kgrid;      // (P+1) x (P+1) argmax on the T-grid (scratch)
+    int32_t d_layout;    // LAYOUT_ROW / LAYOUT_COL / LAYOUT_DENSE
+    int32_t pad;
+};
+
+struct MergeParams {
+    const MergeJob *jobs;  // device array
+    int32_t njobs;
+    int32_t cap;           // K-tiles of a band held in shared memory
+    int64_t n, NT, P;      // P = ceil(n / T): T-grid points 0..P
+    int64_t ld;            // dense leading dimension (elements)
+    int *err;              // device error word
+    int32_t sigma;         // coarse level stride (grid units)
+    int32_t full;          // 1: full-scan coarse level
+    void *dense_out;       // output of LAYOUT_DENSE jobs (per call)
+    int32_t *dense_K;      // optional dense argmax of LAYOUT_DENSE jobs (per call)
+};
+
+// Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full
+// scans) then sigma0/2 .. 1 (windows bounded by the coarser level).
+cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st);
+// Tile refinement + output.
+cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaStream_t st);
+size_t tile_smem_bytes(int in_dtype, int out_dtype, int cap);
+int64_t coarse_sigma0(int64_t P);
+
+// Dense (n+1) x ld matrix -> tile-packed storage in row or column layout.
+cudaError_t launch_pack(const void *src, int dtype, int64_t n, int64_t ld, void *dst, int layout,
+                        cudaStream_t st);
+
+// ------------------------------------------------------------- dense fills
+// Lower triangle (j < i) of a dense matrix outside the diagonal T-tiles gets
+// `lower`; with `fill_upper` the whole upper triangle (j >= i) gets `upper`.
+cudaError_t launch_fill_dense(void *out, int dtype, int64_t n, int64_t ld, int lower, int upper,
+                              int fill_upper, int32_t *K, cudaStream_t st);
+
+// ------------------------------------------------------------- traceback
+struct TbMerge {
+    const void *U;        // upper child (row layout)
+    const void *L;        // lower child (column layout)
+    int32_t in_dtype;
+    int32_t node;         // index of the merged node (its path endpoints)
+    int32_t upper;        // child node indices
+    int32_t lower;
+};
+
+struct TbParams {
+    const TbMerge *merges; // device array (one tree level)
+    int32_t count;
+    int32_t pad;
+    int64_t n, NT;
+    int32_t *pathI;       // [nodes] path endpoints (top vertex i, bottom vertex j)
+    int32_t *pathJ;
+    int64_t *len_out;     // written by the root merge: its maximum (the LCS length)
+    int32_t root_node;
+    int32_t pad2;
+    int *err;
+};
+cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st);
+// pathI[root] = 0, pathJ[root] = n: the whole path, source to sink.
+cudaError_t launch_root_path(int32_t *pathI, int32_t *pathJ, int32_t root, int64_t n, cudaStream_t st);
+
+struct LeafParams {
+    const uint8_t *a;
+    int64_t m;
+    int32_t h, S;
+    const uint8_t *b;
+    int64_t n;
+    const int32_t *pathI; // strip s is node s
+    const int32_t *pathJ;
+    uint32_t *vbuf;       // forward bit-vectors, (n + S + 1) * words
+    int32_t words;
+    int32_t pad;
+    uint8_t *slots;       // [S][h] emitted letters per strip
+    int32_t *counts;      // [S]
+    int32_t *cross;       // nullable [m+1]
+    int *err;
+};
+cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st);
+
+struct CompactParams {
+    const uint8_t *slots;
+    const int32_t *counts;
+    int32_t S, h;
+    uint8_t *out;         // nullable
+    int64_t cap;
+    int64_t *len_out;     // nullable (device)
+    int64_t *len_out2;    // nullable (device, caller's word)
+    int *err;
+};
+cudaError_t launch_compact(const CompactParams &p, cudaStream_t st);
+
+// Copy the internal length word to the caller's word (device to device).
+cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st);
+
+}  // namespace lcsg

@@ -1,0 +1,266 @@
+// strip.cu -- DIST of a strip of h consecutive rows of a, for every source.
+//
+// For one source (top vertex) i the strip's column state after bottom vertex
+// j is F_j(r) = LCS(a_strip[0:r], b[i:j]), r = 0..h.  F_j is nondecreasing in
+// r with steps of 0 or 1, so it is held as an h-bit vector V whose zero bits
+// mark the rows where F steps up.  One column step of the prefix-max
+//     F_j(r) = max(F_j(r-1), F_{j-1}(r), F_{j-1}(r-1) + [a_r = b_j])
+// over all h rows is then (Allison-Dix / Hyyro bit-vector LCS, restated)
+//     u = V & M[b_j];   V' = (V + u) | (V & ~M[b_j]),
+// where M[c] has bit r set iff a_r = c: the carry chain of the integer add
+// carries the running maximum down the rows, and the carry out of the top
+// row is exactly DIST(i, j) - DIST(i, j-1).  The add runs as one
+// add.cc/addc chain over 32-bit words, so 32..256 rows cost a handful of
+// INT32 instructions per (i, j).
+//
+// Work mapping: a warp owns one band of T = 64 sources (2 per lane, two
+// independent dependency chains) and sweeps j across the band's tiles J >= I
+// in lock step, so the match mask of column j is warp-uniform (one broadcast
+// shared-memory load per step).  Each finished T x T tile is staged in shared
+// memory (padded pitch, conflict-free) and written out with coalesced stores
+// in the layout its consumer wants (row or column tile-packed, or dense).
+#include "lcs_common.cuh"
+#include "lcs_kernels.h"
+
+namespace lcsg {
+
+// s = x + y over W words; returns the carry out of the top word.
+template <int W> struct AddChain;
+template <> struct AddChain<1> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[1], const uint32_t (&x)[1],
+                                                   const uint32_t (&y)[1]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, 0, 0;" : "=r"(s[0]), "=r"(c) : "r"(x[0]), "r"(y[0]));
+        return c;
+    }
+};
+template <> struct AddChain<2> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[2], const uint32_t (&x)[2],
+                                                   const uint32_t (&y)[2]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %3, %5;\n\t"
+            "addc.cc.u32 %1, %4, %6;\n\t"
+            "addc.u32 %2, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(y[0]), "r"(y[1]));
+        return c;
+    }
+};
+template <> struct AddChain<4> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[4], const uint32_t (&x)[4],
+                                                   const uint32_t (&y)[4]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %5, %9;\n\t"
+            "addc.cc.u32 %1, %6, %10;\n\t"
+            "addc.cc.u32 %2, %7, %11;\n\t"
+            "addc.cc.u32 %3, %8, %12;\n\t"
+            "addc.u32 %4, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]));
+        return c;
+    }
+};
+template <> struct AddChain<8> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[8], const uint32_t (&x)[8],
+                                                   const uint32_t (&y)[8]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %9, %17;\n\t"
+            "addc.cc.u32 %1, %10, %18;\n\t"
+            "addc.cc.u32 %2, %11, %19;\n\t"
+            "addc.cc.u32 %3, %12, %20;\n\t"
+            "addc.cc.u32 %4, %13, %21;\n\t"
+            "addc.cc.u32 %5, %14, %22;\n\t"
+            "addc.cc.u32 %6, %15, %23;\n\t"
+            "addc.cc.u32 %7, %16, %24;\n\t"
+            "addc.u32 %8, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]),
+              "=r"(s[7]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]),
+              "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]), "r"(y[7]));
+        return c;
+    }
+};
+
+// One column step for one source; returns the increment of DIST.
+template <int W>
+__device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t (&M)[W]) {
+    uint32_t u[W], s[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
+    uint32_t c = AddChain<W>::run(s, V, u);
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = s[w] | (V[w] & ~M[w]);
+    return c;
+}
+
+template <typename OutT>
+struct StagePitch {
+    // Row-layout staging writes 32 lanes x 1 element at rows lane, lane+32 of
+    // one column; a pitch of T + 4/sizeof(OutT) elements puts them in 32
+    // different banks.
+    static constexpr int value = T + 4 / (int)sizeof(OutT);
+};
+
+constexpr int kStripWarps = 4;
+
+template <typename OutT, int W>
+__global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) {
+    constexpr int P = StagePitch<OutT>::value;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *masks = reinterpret_cast<uint32_t *>(smem);             // [256][W]
+    uint32_t *colm_all = masks + 256 * W;                             // [warps][T][W]
+    OutT *stage_all = reinterpret_cast<OutT *>(colm_all + kStripWarps * T * W);  // [warps][T][P]
+
+    const int s = blockIdx.y;
+    const int64_t r0 = (int64_t)s * p.h;
+    const int hs = (int)min((int64_t)p.h, p.m - r0);
+
+    for (int t = threadIdx.x; t < 256 * W; t += blockDim.x) masks[t] = 0u;
+    __syncthreads();
+    for (int r = threadIdx.x; r < hs; r += blockDim.x) {
+        const uint8_t ch = p.a[r0 + r];
+        atomicOr(&masks[ch * W + (r >> 5)], 1u << (r & 31));
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t I = (int64_t)p.band_first + (int64_t)blockIdx.x * kStripWarps + warp;
+    if (I >= p.NT) return;     // no block-wide barrier below this point
+
+    uint32_t *colm = colm_all + warp * T * W;
+    OutT *stage = stage_all + warp * T * P;
+    const int64_t n = p.n;
+    const int64_t i0 = I * T;
+    const int layout = p.dense ? (int)LAYOUT_DENSE : p.outs[s].layout;
+    OutT *out = p.dense ? reinterpret_cast<OutT *>(p.dense) : reinterpret_cast<OutT *>(p.outs[s].base);
+
+    uint32_t VA[W], VB[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) { VA[w] = 0xFFFFFFFFu; VB[w] = 0xFFFFFFFFu; }
+    int dA = 0, dB = 0;
+    const int rA = lane, rB = lane + 32;       // rows of the staged tile
+
+    for (int64_t J = I; J < p.NT; ++J) {
+        const int64_t jb = J * T;
+        // Column masks of this tile: column c consumes letter b[jb + c - 1].
+        for (int c = lane; c < T; c += 32) {
+            const int64_t j = jb + c;
+            if (j >= 1 && j <= n) {
+                const uint8_t ch = p.b[j - 1];
+#pragma unroll
+                for (int w = 0; w < W; ++w) colm[c * W + w] = masks[ch * W + w];
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) colm[c * W + w] = 0u;
+            }
+        }
+        __syncwarp();
+        const int cmax = (int)min((int64_t)T, n + 1 - jb);
+        if (J == I) {
+            // Diagonal tile: source i0+r starts at column r (DIST(i,i) = 0).
+            for (int c = 0; c < cmax; ++c) {
+                uint32_t M[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
+                uint32_t MA[W], MB[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    MA[w] = (c > rA) ? M[w] : 0u;
+                    MB[w] = (c > rB) ? M[w] : 0u;
+                }
+                dA += (int)column_step<W>(VA, MA);
+                dB += (int)column_step<W>(VB, MB);
+                const OutT vA = (c < rA) ? Sentinel<OutT>::value : (OutT)dA;
+                const OutT vB = (c < rB) ? Sentinel<OutT>::value : (OutT)dB;
+                if (layout == LAYOUT_COL) {
+                    stage[c * P + rA] = vA;
+                    stage[c * P + rB] = vB;
+                } else {
+                    stage[rA * P + c] = vA;
+                    stage[rB * P + c] = vB;
+                }
+            }
+        } else {
+            if (layout == LAYOUT_COL) {
+#pragma unroll 4
+                for (int c = 0; c < cmax; ++c) {
+                    uint32_t M[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
+                    dA += (int)column_step<W>(VA, M);
+                    dB += (int)column_step<W>(VB, M);
+                    stage[c * P + rA] = (OutT)dA;
+                    stage[c * P + rB] = (OutT)dB;
+                }
+            } else {
+#pragma unroll 4
+                for (int c = 0; c < cmax; ++c) {
+                    uint32_t M[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
+                    dA += (int)column_step<W>(VA, M);
+                    dB += (int)column_step<W>(VB, M);
+                    stage[rA * P + c] = (OutT)dA;
+                    stage[rB * P + c] = (OutT)dB;
+                }
+            }
+        }
+        __syncwarp();
+        // Write the staged tile out.
+        if (layout == LAYOUT_DENSE) {
+            const int64_t rows = min((int64_t)T, n + 1 - i0);
+            for (int r = 0; r < rows; ++r) {
+                OutT *dst = out + (i0 + r) * p.ld + jb;
+                for (int c = lane; c < cmax; c += 32) dst[c] = stage[r * P + c];
+            }
+        } else {
+            const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, p.NT);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * T2);
+            constexpr int WPR = T * (int)sizeof(OutT) / 4;     // 32-bit words per tile row
+            constexpr int PB = P * (int)sizeof(OutT);          // staged row pitch in bytes
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(stage);
+            for (int w = lane; w < T * WPR; w += 32) {
+                const int r = w / WPR, cw = w - r * WPR;
+                dst[w] = *reinterpret_cast<const uint32_t *>(src + r * PB + cw * 4);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename OutT, int W>
+static cudaError_t launch_t(const StripParams &p, cudaStream_t st) {
+    constexpr int P = StagePitch<OutT>::value;
+    const size_t smem = (size_t)256 * W * 4 + (size_t)kStripWarps * T * W * 4 +
+                        (size_t)kStripWarps * T * P * sizeof(OutT);
+    auto kern = strip_kernel<OutT, W>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t bands = p.NT - p.band_first;
+    dim3 grid((unsigned)ceil_div(bands, kStripWarps), (unsigned)p.S);
+    kern<<<grid, kStripWarps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename OutT>
+static cudaError_t launch_w(const StripParams &p, int words, cudaStream_t st) {
+    switch (words) {
+        case 1: return launch_t<OutT, 1>(p, st);
+        case 2: return launch_t<OutT, 2>(p, st);
+        case 4: return launch_t<OutT, 4>(p, st);
+        case 8: return launch_t<OutT, 8>(p, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_strip(const StripParams &p, int out_dtype, int words, cudaStream_t st) {
+    if (p.NT <= p.band_first || p.S <= 0) return cudaSuccess;
+    switch (out_dtype) {
+        case DT_U8: return launch_w<uint8_t>(p, words, st);
+        case DT_I16: return launch_w<int16_t>(p, words, st);
+        case DT_I32: return launch_w<int32_t>(p, words, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lcsg

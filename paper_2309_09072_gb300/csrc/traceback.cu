@@ -1,0 +1,302 @@
+// traceback.cu -- one LCS from the merge tree (Sec. II-C..II-E).
+//
+// The cross vertex v[r] of row r is the leftmost vertex of the heaviest path
+// in that row (Sec. II-C).  At a tree node covering rows [r0, r1) whose path
+// runs from top vertex i = v[r0] to bottom vertex j, the cross vertex on the
+// boundary row s between its halves is the smallest maximiser
+//     c = min argmax_{i <= k <= j} U(i, k) + L(k, j)
+// (Sec. II-D: it is a by-product of the merge), and the two halves get the
+// sub-paths (i, c) and (c, j).  tb_level_kernel resolves one tree level per
+// launch, top down.  Inside a strip (leaf) the rows are resolved directly:
+// with F(r, c) = LCS(a_strip[0:r], b[i:c]) and B(r, c) = LCS(a_strip[r:h],
+// b[c:j]) from forward and backward bit-vector sweeps, v[r] = min{c : F + B =
+// DIST_strip(i, j)}; letter a_r is marked when the step between the cross
+// vertices of rows r-1 and r gains weight 1 (Sec. II-E).  The marked letters
+// of all strips, in row order, are the LCS.
+#include "lcs_common.cuh"
+#include "lcs_kernels.h"
+
+namespace lcsg {
+
+// ------------------------------------------------------------------ per-level argmax
+__global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
+    __shared__ int sv[8];
+    __shared__ int64_t sk[8];
+    const TbMerge mg = p.merges[blockIdx.x];
+    int64_t i = p.pathI[mg.node], j = p.pathJ[mg.node];
+    if (i < 0 || j > p.n || i > j) {          // never for a consistent tree
+        if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
+        i = 0;
+        j = 0;
+    }
+    int best = INT32_MIN;
+    int64_t bk = INT64_MAX;
+    for (int64_t k = i + threadIdx.x; k <= j; k += blockDim.x) {
+        const int v = load_any(mg.U, row_elem(i, k, p.NT), mg.in_dtype) +
+                      load_any(mg.L, col_elem(k, j), mg.in_dtype);
+        if (v > best) { best = v; bk = k; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const int ov = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        const int64_t ok = __shfl_xor_sync(0xFFFFFFFFu, bk, off);
+        if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] > best || (sv[w] == best && sk[w] < bk)) { best = sv[w]; bk = sk[w]; }
+        const int32_t c = (int32_t)bk;
+        p.pathI[mg.upper] = (int32_t)i;
+        p.pathJ[mg.upper] = c;
+        p.pathI[mg.lower] = c;
+        p.pathJ[mg.lower] = (int32_t)j;
+        if (mg.node == p.root_node && p.len_out) *p.len_out = best;
+    }
+}
+
+__global__ void root_path_kernel(int32_t *pI, int32_t *pJ, int32_t root, int32_t n) {
+    pI[root] = 0;
+    pJ[root] = n;
+}
+
+cudaError_t launch_root_path(int32_t *pathI, int32_t *pathJ, int32_t root, int64_t n, cudaStream_t st) {
+    root_path_kernel<<<1, 1, 0, st>>>(pathI, pathJ, root, (int32_t)n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st) {
+    if (p.count <= 0) return cudaSuccess;
+    tb_level_kernel<<<(unsigned)p.count, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ leaves
+template <int W>
+__device__ __forceinline__ uint32_t add_chain(uint32_t (&s)[W], const uint32_t (&x)[W], const uint32_t (&y)[W]) {
+    // Multi-word add with carry out (portable form; the leaf sweep is short).
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint64_t t = (uint64_t)x[w] + (uint64_t)y[w] + c;
+        s[w] = (uint32_t)t;
+        c = (uint32_t)(t >> 32);
+    }
+    return c;
+}
+
+template <int W>
+__device__ __forceinline__ void leaf_step(uint32_t (&V)[W], const uint32_t *M) {
+    uint32_t u[W], s[W], m[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) { m[w] = M[w]; u[w] = V[w] & m[w]; }
+    add_chain<W>(s, V, u);
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = s[w] | (V[w] & ~m[w]);
+}
+
+// Number of zero bits among bits [0, r) of the W-word vector at v.
+template <int W>
+__device__ __forceinline__ int zeros_below(const uint32_t (&v)[W], int r) {
+    int ones = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int lo = w * 32;
+        if (r >= lo + 32) ones += __popc(v[w]);
+        else if (r > lo) ones += __popc(v[w] & ((1u << (r - lo)) - 1u));
+    }
+    return r - ones;
+}
+
+constexpr int kLeafWarps = 2;
+
+template <int W>
+__global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_warp_words = 2 * 256 * W + 2 * 260;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem) + warp * per_warp_words;   // [256][W]
+    uint32_t *bm = fm + 256 * W;                                                  // [256][W]
+    int32_t *vv = reinterpret_cast<int32_t *>(bm + 256 * W);                     // [h+1]
+    int32_t *Fv = vv + 260;                                                       // [h+1]
+    const int s = blockIdx.x * kLeafWarps + warp;
+    if (s >= p.S) return;
+    const int64_t r0 = (int64_t)s * p.h;
+    const int hs = (int)min((int64_t)p.h, p.m - r0);
+    const int64_t i = p.pathI[s], j = p.pathJ[s];
+
+    for (int t = lane; t < 256 * W; t += 32) { fm[t] = 0u; bm[t] = 0u; }
+    __syncwarp();
+    for (int r = lane; r < hs; r += 32) {
+        const uint8_t ch = p.a[r0 + r];
+        atomicOr(&fm[ch * W + (r >> 5)], 1u << (r & 31));
+        const int rr = hs - 1 - r;                       // reversed row order
+        atomicOr(&bm[ch * W + (rr >> 5)], 1u << (rr & 31));
+    }
+    __syncwarp();
+    if (i < 0 || j < i || j > p.n) {
+        if (lane == 0) { set_error(p.err, ERR_BOUNDS); p.counts[s] = 0; }
+        return;
+    }
+
+    // Forward sweep from source i; V_c stored for c = i..j.
+    uint32_t *vb = p.vbuf + (i + s) * (int64_t)W;
+    uint32_t V[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
+    if (lane < W) vb[lane] = 0xFFFFFFFFu;
+    for (int64_t c = i + 1; c <= j; ++c) {
+        leaf_step<W>(V, fm + p.b[c - 1] * W);
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w) vb[(c - i) * W + w] = V[w];
+    }
+    int ones = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) ones += __popc(V[w]);
+    const int Ltot = 32 * W - ones;               // padding bits stay 1
+    __syncwarp();
+
+    // Backward sweep from sink j; rows r = lane + 32 q.
+    const int nq = (hs + 1 + 31) / 32;
+    uint32_t Wv[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) Wv[w] = 0xFFFFFFFFu;
+    int vloc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) vloc[q] = -1;
+    for (int64_t c = j; c >= i; --c) {
+        uint32_t Vc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) Vc[w] = vb[(c - i) * W + w];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (q >= nq) break;
+            const int r = lane + 32 * q;
+            if (r > hs) continue;
+            const int F = zeros_below<W>(Vc, r);
+            const int B = zeros_below<W>(Wv, hs - r);
+            if (F + B == Ltot) vloc[q] = (int)c;
+        }
+        if (c > i) leaf_step<W>(Wv, bm + p.b[c - 1] * W);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        if (q >= nq) break;
+        const int r = lane + 32 * q;
+        if (r > hs) continue;
+        const int c = vloc[q];
+        vv[r] = c;
+        uint32_t Vc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) Vc[w] = (c >= i) ? vb[(c - i) * W + w] : 0u;
+        Fv[r] = (c >= i) ? zeros_below<W>(Vc, r) : -1000000;
+    }
+    __syncwarp();
+    // Marks, in row order.
+    int base = 0;
+    for (int q = 0; q < nq; ++q) {
+        const int r = lane + 32 * q;
+        bool mark = false;
+        if (r >= 1 && r <= hs) mark = (Fv[r] - Fv[r - 1]) == 1;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, mark);
+        if (mark) {
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            p.slots[(int64_t)s * p.h + pos] = p.a[r0 + r - 1];
+        }
+        base += __popc(bal);
+    }
+    if (lane == 0) {
+        p.counts[s] = base;
+        // Interior strips end at the next strip's cross vertex; the last strip
+        // ends at the sink (m, n), which need not be the cross vertex of row m.
+        if (base != Ltot || vv[0] != i || (s < p.S - 1 && vv[hs] != j)) set_error(p.err, ERR_BOUNDS);
+    }
+    if (p.cross) {
+        const bool last = (s == p.S - 1);
+        for (int r = lane; r < hs + (last ? 1 : 0); r += 32) p.cross[r0 + r] = vv[r];
+    }
+}
+
+template <int W>
+static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
+    const size_t smem = (size_t)kLeafWarps * (2 * 256 * W + 2 * 260) * 4;
+    auto kern = leaf_kernel<W>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ceil_div(p.S, kLeafWarps), kLeafWarps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st) {
+    if (p.S <= 0) return cudaSuccess;
+    switch (p.words) {
+        case 1: return launch_leaf_t<1>(p, st);
+        case 2: return launch_leaf_t<2>(p, st);
+        case 4: return launch_leaf_t<4>(p, st);
+        case 8: return launch_leaf_t<8>(p, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ compaction
+__global__ void __launch_bounds__(1024) compact_kernel(CompactParams p, int32_t *offsets) {
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Exclusive scan of counts in chunks of 1024.
+    for (int base = 0; base < p.S; base += 1024) {
+        const int s = base + threadIdx.x;
+        const int v = (s < p.S) ? p.counts[s] : 0;
+        int x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_sums[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+                if (lane >= off) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0);
+        if (s < p.S) offsets[s] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    const int64_t total = carry;
+    if (threadIdx.x == 0) {
+        if (p.len_out) *p.len_out = total;
+        if (p.len_out2) *p.len_out2 = total;
+        if (p.out && total > p.cap) set_error(p.err, ERR_OVERFLOW);
+    }
+    if (!p.out || total > p.cap) return;
+    for (int s = warp; s < p.S; s += 32) {
+        const int cnt = p.counts[s], off = offsets[s];
+        for (int t = lane; t < cnt; t += 32) p.out[off + t] = p.slots[(int64_t)s * p.h + t];
+    }
+}
+
+cudaError_t launch_compact(const CompactParams &p, cudaStream_t st) {
+    // offsets live right after the counts array (the planner reserves 2*S ints).
+    compact_kernel<<<1, 1024, 0, st>>>(p, const_cast<int32_t *>(p.counts) + p.S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace lcsg
