@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the DIST hot path: one step = the whole path on one pair.
+
+Workload: one pair m = n = 4096 over ACGT (i.i.d. by default, or the
+correlated variant), full int32 DIST of the whole grid + LCS length + one LCS
+by leftmost-argmax traceback.  Metric: GCUPS = m*n cells per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one process per GPU; every rank solves its own
+pair of the same workload (independent problems, no data-path collective) and
+the value is all ranks' cells over the slowest rank's time ("weak" scaling).
+The reference arm times the CPU oracle (the only implementation of the
+method besides ours) on the host cores, on a bounded sample of each step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS (m·n/s) per pair"
+UNIT = "GCUPS"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=["iid", "correlated"], default="iid")
+    ap.add_argument("--strip-height", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload(variant, rank):
+    from paper_2309_09072_gb300 import inputs
+    a, b = inputs.pair_4096(variant, seed=1 + rank)
+    return a, b
+
+
+def config_dict(variant, m, n, h):
+    return {"workload": "single pair m=n=4096, ACGT %s: int32 DIST of the whole grid + LCS length + "
+                        "leftmost-argmax LCS" % variant,
+            "m": m, "n": n, "variant": variant, "dist_dtype": "int32", "strip_height": h,
+            "l2": "flushed between steps (256 MiB write outside the timed events)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.4)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(a, b, stride, nthreads=0):
+    """Time the oracle on every stride-th DIST row plus the full traceback and
+    extrapolate to the whole step (all n+1 rows).  Returns (seconds, threads)."""
+    import numpy as np
+    import oracle
+    n = len(b)
+    rows = np.arange(0, n + 1, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.dist_rows(a, b, rows, nthreads)
+    t1 = time.perf_counter()
+    oracle.traceback(a, b)
+    t2 = time.perf_counter()
+    threads = nthreads or os.cpu_count() or 1
+    return (t1 - t0) * (n + 1) / len(rows) + (t2 - t1), threads
+
+
+def cpu_baseline(a, b, stride=4):
+    m, n = len(a), len(b)
+    t, threads = oracle_sample(a, b, stride)
+    return {"value": m * n / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "oracle per-source DIST on every %dth of the %d rows (all host threads), "
+                      "extrapolated to all rows, plus the full O(mn) leftmost traceback" % (stride, n + 1)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    a, b = workload(args.variant, 0)
+    m, n = len(a), len(b)
+    stride = 32
+    for _ in range(args.warmup):
+        oracle_sample(a, b, stride)
+    total = 0.0
+    threads = 1
+    for _ in range(args.steps):
+        t, threads = oracle_sample(a, b, stride)
+        total += t
+    ms = total / args.steps * 1e3
+    value = m * n * args.steps / total / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_dict(args.variant, m, n, 0), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "per step: oracle DIST on every %dth row (extrapolated to all rows) + "
+                                       "full traceback" % stride},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def roofline(profile, peaks, peaks_src, int_peak):
+    """Dominant kernel (largest share of device time) against its bound."""
+    if not profile:
+        return None
+    kind, p = max(profile.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = p["ms"] / p["launches"]
+    share = p["ms"] / sum(v["ms"] for v in profile.values())
+    if kind == "strip":
+        achieved = p["ops"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
+        return {"kernel": kind, "bound": "alu", "achieved": achieved, "peak": int_peak["derived_gops"],
+                "unit": "Gop/s", "frac": achieved / int_peak["derived_gops"], "traffic": None,
+                "peak_source": "152 SMs x 128 INT32 lanes/clk x 2070 MHz (derived)",
+                "measured_int32_gops": int_peak["measured_gops"], "share_of_device_time": share,
+                "ms_per_launch": per_launch_ms, "launches": p["launches"]}
+    achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": "hbm_gbs of %s" % peaks_src,
+            "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"]}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2309_09072_gb300 import binding as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    a, b = workload(args.variant, rank)
+    m, n = len(a), len(b)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    ctx = B.lcs_create(local, 0)
+    B.lcs_set_strip_height(ctx, args.strip_height)
+    ad = torch.from_numpy(a.copy()).to(dev)
+    bd = torch.from_numpy(b.copy()).to(dev)
+    ld = ((n + 1) * 4 + 15) // 16 * 16 // 4
+    dist_out = torch.empty((n + 1, ld), dtype=torch.int32, device=dev)
+    lcs_out = torch.empty(min(m, n), dtype=torch.uint8, device=dev)
+    len_out = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        B.lcs_solve(ctx, ad, bd, dist=dist_out, out_lcs=lcs_out, out_len=len_out, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    B.lcs_sync(ctx, stream)
+    stats = B.lcs_get_stats(ctx)
+    int_gops, int_mhz = B.lcs_measure_int32_peak(local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    int_peak = {"measured_gops": int_gops, "measured_mhz": int_mhz,
+                "derived_gops": sms * 128 * 2070e6 / 1e9}
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    B.lcs_set_profiling(ctx, True)
+    clocks = ClockSampler(local)
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    B.lcs_sync(ctx, stream)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    profile = B.lcs_get_profile(ctx)
+    B.lcs_set_profiling(ctx, False)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * m * n * args.steps / (total_ms * 1e-3) / 1e9
+
+    # End to end through the public host API: H2D of a, b and D2H of DIST,
+    # the LCS and the length every step.
+    ah = torch.from_numpy(a.copy()).pin_memory()
+    bh = torch.from_numpy(b.copy()).pin_memory()
+    dh = torch.empty((n + 1, ld), dtype=torch.int32).pin_memory()
+    lh = torch.empty(min(m, n), dtype=torch.uint8).pin_memory()
+    L = 0
+    for _ in range(2):
+        L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh, stream=stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * m * n * args.e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": m + n, "d2h_bytes_per_step": (n + 1) * (n + 1) * 4 + L + 16,
+           "steps": args.e2e_steps, "api": "lcs_solve_host (pinned host buffers)"}
+
+    peaks, peaks_src = load_peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_dict(args.variant, m, n, stats["strip_height"]),
+            "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
+            "roofline": roofline(profile, peaks, peaks_src, int_peak),
+            "clocks": clock_info,
+            "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
+            "lcs_length": L, "workspace_bytes": stats["peak_workspace_bytes"]}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, b)
+    B.lcs_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,6 +84,21 @@ typedef struct {
     int32_t tile;                   /* merge tile edge (vertices)                */
 } lcs_stats;
 
+/* Per-kernel-class timing of the calls made while profiling is on
+ * (lcs_set_profiling).  Kinds: 0 strip builder, 1 coarse argmax grid,
+ * 2 merge tile refinement, 3 traceback level argmax, 4 traceback leaves,
+ * 5 compaction, 6 dense fills / packing.  `ms` is the summed device time of
+ * the launches measured with CUDA events on the launching stream; `bytes`
+ * and `ops` are the algorithmic DRAM bytes and INT32 word operations of
+ * those launches (see lcs_get_profile). */
+typedef struct {
+    int32_t kind;
+    int32_t launches;
+    double ms;
+    double bytes;
+    double ops;
+} lcs_kernel_profile;
+
 /* Create a context on CUDA device `device`.  mem_budget_bytes caps the
  * workspace (0 = 64 GiB).  No device memory is allocated until the first
  * call that needs it.  *out receives the context.
@@ -107,6 +122,26 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
 
 /* Counters of the last call (see lcs_stats).  Errors: EINVAL. */
 lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out);
+
+/* Turn per-launch event timing on (1) or off (0); turning it on clears the
+ * accumulated profile.  Adds two event records per launch.  Errors: EINVAL. */
+lcs_status lcs_set_profiling(lcs_ctx *ctx, int32_t enable);
+
+/* Synchronise the device and return the accumulated profile, one entry per
+ * kernel kind that launched (at most cap entries; *count receives the
+ * number written), then clear it.  Algorithmic bytes: strip builder = the
+ * DIST tiles it writes; merge tile = both operand triangles read once plus
+ * the output triangle written once, (n+1)(n+2)/2 entries each.  Algorithmic
+ * ops (strip builder) = per (strip, source i, column j > i) step, 3 integer
+ * instructions per 32-bit word of the strip's bit vector (and, add with
+ * carry, and-not/or) plus 2 (carry out, accumulate).  Errors: EINVAL, ECUDA. */
+lcs_status lcs_get_profile(lcs_ctx *ctx, lcs_kernel_profile *out, int32_t cap, int32_t *count);
+
+/* Measured INT32 ALU throughput of the device: a kernel of independent
+ * 32-bit integer add/logic operations filling every SM, timed with events.
+ * *gops_out receives 10^9 operations per second; *sm_mhz_out (nullable)
+ * the SM clock the kernel's own timer saw.  Errors: EINVAL, ECUDA. */
+lcs_status lcs_measure_int32_peak(int device, double *gops_out, double *sm_mhz_out);
 
 /* Synchronise `stream` and report device-side failures of earlier
  * asynchronous calls on ctx (ETIMEOUT from a bounded wait, EOVERFLOW from a

@@ -40,6 +40,19 @@ class lcs_stats(ctypes.Structure):
     ]
 
 
+class lcs_kernel_profile(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+        ("bytes", ctypes.c_double),
+        ("ops", ctypes.c_double),
+    ]
+
+
+KERNEL_KINDS = {0: "strip", 1: "coarse", 2: "merge_tile", 3: "traceback_level", 4: "traceback_leaf",
+                5: "compact", 6: "fill"}
+
 _lib = None
 _lock = threading.Lock()
 
@@ -73,6 +86,10 @@ def load(path: str = LIB_PATH):
             "lcs_set_strip_height": ([vp, i32], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
             "lcs_sync": ([vp, vp], st),
+            "lcs_set_profiling": ([vp, i32], st),
+            "lcs_get_profile": ([vp, ctypes.POINTER(lcs_kernel_profile), i32, ctypes.POINTER(i32)], st),
+            "lcs_measure_int32_peak": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)], st),
             "lcs_strip_dist": ([vp, vp, i32, vp, i64, st, vp, i64, vp], st),
             "lcs_merge": ([vp, vp, vp, i64, st, i64, vp, vp, vp], st),
             "lcs_dist": ([vp, vp, i64, vp, i64, st, vp, i64, vp], st),
@@ -162,6 +179,30 @@ def lcs_get_stats(ctx) -> dict:
     s = lcs_stats()
     _check(ctx, load().lcs_get_stats(ctx, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def lcs_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load().lcs_set_profiling(ctx, 1 if enable else 0))
+
+
+def lcs_get_profile(ctx) -> dict:
+    """{kind name: {launches, ms, bytes, ops}} accumulated since profiling was enabled."""
+    arr = (lcs_kernel_profile * 8)()
+    cnt = ctypes.c_int32()
+    _check(ctx, load().lcs_get_profile(ctx, arr, 8, ctypes.byref(cnt)))
+    out = {}
+    for k in range(cnt.value):
+        e = arr[k]
+        out[KERNEL_KINDS.get(e.kind, str(e.kind))] = {"launches": e.launches, "ms": e.ms, "bytes": e.bytes,
+                                                      "ops": e.ops}
+    return out
+
+
+def lcs_measure_int32_peak(device: int = 0):
+    """(10^9 INT32 ops/s, SM MHz seen by the kernel)."""
+    g, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(None, load().lcs_measure_int32_peak(int(device), ctypes.byref(g), ctypes.byref(mhz)))
+    return g.value, mhz.value
 
 
 def lcs_sync(ctx, stream=None) -> None:

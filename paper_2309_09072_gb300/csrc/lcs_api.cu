@@ -38,7 +38,6 @@ int words_for(int h) {
     return w <= 1 ? 1 : (w <= 2 ? 2 : (w <= 4 ? 4 : 8));
 }
 
-int tile_cap(int in_dt) { return in_dt == DT_U8 ? 8 : (in_dt == DT_I16 ? 4 : 2); }
 
 struct Node {
     int64_t row0 = 0, rows = 0;
@@ -98,6 +97,11 @@ struct lcs_ctx {
     Plan plan;
     bool plan_uploaded = false;
     int launches = 0;
+    // profiling (lcs_set_profiling)
+    bool profiling = false;
+    struct Rec { int kind; cudaEvent_t e0, e1; double bytes, ops; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace {
@@ -119,11 +123,50 @@ lcs_status cuda_fail(lcs_ctx *ctx, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
     } while (0)
 
-#define LCS_LAUNCH(ctx, expr)                                  \
-    do {                                                       \
-        cudaError_t e_ = (expr);                               \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
-        (ctx)->launches++;                                     \
+enum Kind { K_STRIP = 0, K_COARSE = 1, K_TILE = 2, K_TB = 3, K_LEAF = 4, K_COMPACT = 5, K_FILL = 6, K_KINDS = 7 };
+
+double tri_entries(int64_t n) { return (double)(n + 1) * (double)(n + 2) / 2.0; }
+// Strip builder: per (strip, source i, column j > i) step, 3 integer
+// instructions per 32-bit word (and, add with carry, and-not/or) plus 2
+// (carry out, accumulate).
+double strip_ops(int strips, int64_t n, int words) {
+    return (double)strips * (double)n * (double)(n + 1) / 2.0 * (3.0 * words + 2.0);
+}
+
+cudaEvent_t take_event(lcs_ctx *ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Event pair around one launch when profiling is on (else a no-op).
+int prof_begin(lcs_ctx *ctx, cudaStream_t st) {
+    if (!ctx->profiling) return -1;
+    lcs_ctx::Rec r{0, take_event(ctx), take_event(ctx), 0.0, 0.0};
+    if (!r.e0 || !r.e1) return -1;
+    cudaEventRecord(r.e0, st);
+    ctx->recs.push_back(r);
+    return (int)ctx->recs.size() - 1;
+}
+void prof_end(lcs_ctx *ctx, int idx, cudaStream_t st, int kind, double bytes, double ops) {
+    if (idx < 0) return;
+    lcs_ctx::Rec &r = ctx->recs[idx];
+    r.kind = kind; r.bytes = bytes; r.ops = ops;
+    cudaEventRecord(r.e1, st);
+}
+
+#define LCS_LAUNCHK(ctx, st, kind, bytes, ops, expr)              \
+    do {                                                          \
+        const int pi_ = prof_begin(ctx, st);                      \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);  \
+        (ctx)->launches++;                                        \
+        prof_end(ctx, pi_, st, kind, bytes, ops);                 \
     } while (0)
 
 int auto_strip_height(int64_t m, int64_t n) {
@@ -198,7 +241,7 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         Node &nd = P.nodes[v];
         if (nd.root) continue;
         nd.off = off;
-        off = align256(off + (size_t)tiles * T2 * dt_size(nd.dtype));
+        off = align256(off + (size_t)tiles * tile_elems(nd.dtype) * dt_size(nd.dtype));
     }
     for (auto &mg : P.merges) {
         mg.kgrid_off = off;
@@ -388,7 +431,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         lcs_status s = ensure_workspace(ctx, std::max(ctx->ws_bytes, kHeaderBytes));
         if (s != LCS_OK) return s;
         if (dist) {
-            LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 1,
+            LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 1,
                                               nullptr, st));
         }
         LCS_CK(ctx, cudaMemsetAsync(len_word(ctx), 0, sizeof(int64_t), st));
@@ -418,9 +461,9 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             StripParams sp{};
             sp.a = a; sp.m = m; sp.h = P.h; sp.S = 1; sp.b = b; sp.n = n; sp.NT = P.NT;
             sp.outs = nullptr; sp.dense = dist; sp.ld = ld; sp.band_first = 0;
-            LCS_LAUNCH(ctx, launch_strip(sp, rdt, P.words, st));
+            LCS_LAUNCHK(ctx, st, K_STRIP, tri_entries(n) * dt_size(rdt), strip_ops(1, n, P.words), launch_strip(sp, rdt, P.words, st));
             if (P.NT > 1)
-                LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
                                                   nullptr, st));
         }
     } else {
@@ -438,7 +481,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             }
             if (!any) continue;
             if (all) {
-                LCS_LAUNCH(ctx, launch_strip(sp, dt, P.words, st));
+                LCS_LAUNCHK(ctx, st, K_STRIP, P.S * tri_entries(n) * dt_size(dt), strip_ops(P.S, n, P.words), launch_strip(sp, dt, P.words, st));
             } else {
                 for (int q = 0; q < P.S; ++q) {
                     if (P.nodes[q].dtype != dt) continue;
@@ -447,7 +490,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                     one.m = P.nodes[q].rows;
                     one.S = 1;
                     one.outs = sp.outs + q;
-                    LCS_LAUNCH(ctx, launch_strip(one, dt, P.words, st));
+                    LCS_LAUNCHK(ctx, st, K_STRIP, tri_entries(n) * dt_size(dt), strip_ops(1, n, P.words), launch_strip(one, dt, P.words, st));
                 }
             }
         }
@@ -458,53 +501,54 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             MergeParams mp{};
             mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
             mp.njobs = g.count;
-            mp.cap = tile_cap(g.in_dt);
             mp.n = n; mp.NT = P.NT; mp.P = P.P; mp.ld = ld; mp.err = err;
             mp.dense_out = g.root ? dist : nullptr;
             mp.dense_K = nullptr;
             mp.sigma = (int32_t)sigma0; mp.full = 1;
-            LCS_LAUNCH(ctx, launch_coarse(mp, g.in_dt, st));
+            LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
                 mp.sigma = (int32_t)sg; mp.full = 0;
-                LCS_LAUNCH(ctx, launch_coarse(mp, g.in_dt, st));
+                LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             }
-            LCS_LAUNCH(ctx, launch_tile(mp, g.in_dt, g.out_dt, st));
+            LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)), 0.0,
+                        launch_tile_pair(mp, g.in_dt, g.out_dt, st));
+            ctx->launches++;   // the pair is two kernel launches
             if (g.root)
-                LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
                                                   nullptr, st));
         }
     }
 
     // 3. traceback / length
     if (want_tb || (want_len && P.S == 1)) {
-        LCS_LAUNCH(ctx, launch_root_path(pathI, pathJ, P.root, n, st));
+        LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_root_path(pathI, pathJ, P.root, n, st));
         const TbMerge *tbd = reinterpret_cast<const TbMerge *>(base + P.off_tb);
         for (auto &lv : P.tb_levels) {
             TbParams tp{};
             tp.merges = tbd + lv.first; tp.count = lv.second;
             tp.n = n; tp.NT = P.NT; tp.pathI = pathI; tp.pathJ = pathJ;
             tp.len_out = nullptr; tp.root_node = P.root; tp.err = err;
-            LCS_LAUNCH(ctx, launch_tb_level(tp, st));
+            LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
         }
         LeafParams lp{};
         lp.a = a; lp.m = m; lp.h = P.h; lp.S = P.S; lp.b = b; lp.n = n;
         lp.pathI = pathI; lp.pathJ = pathJ;
         lp.vbuf = reinterpret_cast<uint32_t *>(base + P.off_vbuf);
         lp.words = P.words; lp.slots = slots; lp.counts = counts; lp.cross = cross; lp.err = err;
-        LCS_LAUNCH(ctx, launch_leaf(lp, st));
+        LCS_LAUNCHK(ctx, st, K_LEAF, 0.0, 0.0, launch_leaf(lp, st));
         CompactParams cp{};
         cp.slots = slots; cp.counts = counts; cp.S = P.S; cp.h = P.h;
         cp.out = out_lcs; cp.cap = cap; cp.len_out = len_word(ctx); cp.len_out2 = len_dev_out; cp.err = err;
-        LCS_LAUNCH(ctx, launch_compact(cp, st));
+        LCS_LAUNCHK(ctx, st, K_COMPACT, 0.0, 0.0, launch_compact(cp, st));
     } else if (want_len) {
         // Root maximum only: the first traceback level.
-        LCS_LAUNCH(ctx, launch_root_path(pathI, pathJ, P.root, n, st));
+        LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_root_path(pathI, pathJ, P.root, n, st));
         const TbMerge *tbd = reinterpret_cast<const TbMerge *>(base + P.off_tb);
         TbParams tp{};
         tp.merges = tbd + P.tb_levels[0].first; tp.count = P.tb_levels[0].second;
         tp.n = n; tp.NT = P.NT; tp.pathI = pathI; tp.pathJ = pathJ;
         tp.len_out = len_word(ctx); tp.root_node = P.root; tp.err = err;
-        LCS_LAUNCH(ctx, launch_tb_level(tp, st));
+        LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
         if (len_dev_out) LCS_CK(ctx, launch_copy_len(len_word(ctx), len_dev_out, st));
     }
     ctx->stats.strip_height = P.h;
@@ -557,6 +601,8 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
+    for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
     return LCS_OK;
 }
@@ -590,6 +636,39 @@ lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out) {
     return LCS_OK;
 }
 
+lcs_status lcs_set_profiling(lcs_ctx *ctx, int32_t enable) {
+    if (!ctx) return LCS_EINVAL;
+    cudaDeviceSynchronize();
+    for (auto &r : ctx->recs) { ctx->pool.push_back(r.e0); ctx->pool.push_back(r.e1); }
+    ctx->recs.clear();
+    ctx->profiling = enable != 0;
+    return LCS_OK;
+}
+
+lcs_status lcs_get_profile(lcs_ctx *ctx, lcs_kernel_profile *out, int32_t cap, int32_t *count) {
+    if (!ctx || !count || (cap > 0 && !out)) return LCS_EINVAL;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    LCS_CK(ctx, cudaDeviceSynchronize());
+    lcs_kernel_profile acc[K_KINDS];
+    for (int k = 0; k < K_KINDS; ++k) acc[k] = lcs_kernel_profile{k, 0, 0.0, 0.0, 0.0};
+    for (auto &r : ctx->recs) {
+        float ms = 0.f;
+        LCS_CK(ctx, cudaEventElapsedTime(&ms, r.e0, r.e1));
+        acc[r.kind].launches += 1;
+        acc[r.kind].ms += ms;
+        acc[r.kind].bytes += r.bytes;
+        acc[r.kind].ops += r.ops;
+        ctx->pool.push_back(r.e0);
+        ctx->pool.push_back(r.e1);
+    }
+    ctx->recs.clear();
+    int c = 0;
+    for (int k = 0; k < K_KINDS; ++k)
+        if (acc[k].launches > 0 && c < cap) out[c++] = acc[k];
+    *count = c;
+    return LCS_OK;
+}
+
 lcs_status lcs_sync(lcs_ctx *ctx, void *stream) {
     if (!ctx) return LCS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -616,9 +695,9 @@ lcs_status lcs_strip_dist(lcs_ctx *ctx, const uint8_t *a_strip, int32_t h, const
     StripParams sp{};
     sp.a = a_strip; sp.m = h; sp.h = h; sp.S = 1; sp.b = b; sp.n = n; sp.NT = num_tiles_side(n);
     sp.outs = nullptr; sp.dense = dist; sp.ld = ld; sp.band_first = 0;
-    LCS_LAUNCH(ctx, launch_strip(sp, rdt, words_for(h), st));
+    LCS_LAUNCHK(ctx, st, K_STRIP, tri_entries(n) * dt_size(rdt), strip_ops(1, n, words_for(h)), launch_strip(sp, rdt, words_for(h), st));
     if (sp.NT > 1)
-        LCS_LAUNCH(ctx, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, nullptr, st));
+        LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, nullptr, st));
     ctx->stats.kernel_launches = ctx->launches;
     return LCS_OK;
 }
@@ -638,7 +717,7 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
     if (dist_out == dist_u || dist_out == dist_l) return fail(ctx, LCS_EINVAL, "dist_out aliases an input");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t NT = num_tiles_side(n), P = ceil_div(n, T);
-    const size_t packed = align256((size_t)num_tiles_tri(NT) * T2 * dt_size(dt));
+    const size_t packed = align256((size_t)num_tiles_tri(NT) * tile_elems(dt) * dt_size(dt));
     const size_t kg = align256((size_t)(P + 1) * (P + 1) * 4);
     const size_t need = kHeaderBytes + 2 * packed + kg + align256(sizeof(MergeJob));
     if ((s = ensure_workspace(ctx, std::max(ctx->ws_bytes, kHeaderBytes))) != LCS_OK) return s;
@@ -647,24 +726,25 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
     char *Up = io + kHeaderBytes, *Lp = Up + packed;
     int32_t *kgrid = reinterpret_cast<int32_t *>(Lp + packed);
     MergeJob *jobd = reinterpret_cast<MergeJob *>(Lp + packed + kg);
-    LCS_LAUNCH(ctx, launch_pack(dist_u, dt, n, ld, Up, LAYOUT_ROW, st));
-    LCS_LAUNCH(ctx, launch_pack(dist_l, dt, n, ld, Lp, LAYOUT_COL, st));
+    LCS_LAUNCHK(ctx, st, K_FILL, 0.0, 0.0, launch_pack(dist_u, dt, n, ld, Up, LAYOUT_ROW, st));
+    LCS_LAUNCHK(ctx, st, K_FILL, 0.0, 0.0, launch_pack(dist_l, dt, n, ld, Lp, LAYOUT_COL, st));
     MergeJob job{};
     job.U = Up; job.L = Lp; job.D = nullptr; job.kgrid = kgrid; job.d_layout = LAYOUT_DENSE;
     LCS_CK(ctx, cudaMemcpyAsync(jobd, &job, sizeof(job), cudaMemcpyHostToDevice, st));
     MergeParams mp{};
-    mp.jobs = jobd; mp.njobs = 1; mp.cap = tile_cap(dt);
+    mp.jobs = jobd; mp.njobs = 1;
     mp.n = n; mp.NT = NT; mp.P = P; mp.ld = ld; mp.err = err_word(ctx);
     mp.dense_out = dist_out; mp.dense_K = argmax_out;
     const int64_t sigma0 = coarse_sigma0(std::max<int64_t>(P, 1));
     mp.sigma = (int32_t)sigma0; mp.full = 1;
-    LCS_LAUNCH(ctx, launch_coarse(mp, dt, st));
+    LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, dt, st));
     for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
         mp.sigma = (int32_t)sg; mp.full = 0;
-        LCS_LAUNCH(ctx, launch_coarse(mp, dt, st));
+        LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, dt, st));
     }
-    LCS_LAUNCH(ctx, launch_tile(mp, dt, dt, st));
-    LCS_LAUNCH(ctx, launch_fill_dense(dist_out, dt, n, ld, dt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, argmax_out, st));
+    LCS_LAUNCHK(ctx, st, K_TILE, tri_entries(n) * 3.0 * dt_size(dt), 0.0, launch_tile_pair(mp, dt, dt, st));
+    ctx->launches++;
+    LCS_LAUNCHK(ctx, st, K_FILL, 0.0, 0.0, launch_fill_dense(dist_out, dt, n, ld, dt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0, argmax_out, st));
     // The job descriptor lives on the host stack: make sure the copy is done.
     LCS_CK(ctx, cudaStreamSynchronize(st));
     ctx->stats.kernel_launches = ctx->launches;

@@ -1,7 +1,10 @@
 // lcs_common.cuh -- layout, types and PTX helpers shared by the GB300 kernels.
 //
 // Internal DIST storage ("tile-packed").  A DIST matrix over vertices 0..n is
-// cut into T x T tiles (T = 64); only tiles (I, J) with I <= J exist.  A node
+// cut into T x T tiles (T = 64); only tiles (I, J) with I <= J exist.  Each
+// stored tile has a row pitch of T + 4/sizeof(element) elements: 4 bytes of
+// padding per row make rows that are 2 apart fall into different shared-
+// memory banks once a tile is copied byte for byte into shared memory.  A node
 // that the merge above it reads by ROWS (the upper operand U) is stored in
 // row layout: tiles ordered by I then J, each tile row-major (i-major).  A
 // node read by COLUMNS (the lower operand L) is stored in column layout:
@@ -37,13 +40,24 @@ __host__ __device__ inline int64_t row_tile(int64_t I, int64_t J, int64_t NT) {
 // Column layout: tile (I <= J, J) -> J*(J+1)/2 + I.
 __host__ __device__ inline int64_t col_tile(int64_t I, int64_t J) { return J * (J + 1) / 2 + I; }
 
+__host__ __device__ inline int dt_bytes(int dt) { return dt == 2 ? 1 : (dt == 1 ? 2 : 4); }
+// Stored tile: T rows of pitch T + 4/size elements.
+__host__ __device__ inline int tile_pitch(int dt) { return T + 4 / dt_bytes(dt); }
+__host__ __device__ inline int64_t tile_elems(int dt) { return (int64_t)T * tile_pitch(dt); }
+template <typename V> struct Fmt {
+    static constexpr int P = T + 4 / (int)sizeof(V);
+    static constexpr int ELEMS = T * P;
+};
+
 // Element (i, k) of a row-layout matrix, k >= i.
+template <typename V>
 __device__ __forceinline__ int64_t row_elem(int64_t i, int64_t k, int64_t NT) {
-    return row_tile(i >> T_SHIFT, k >> T_SHIFT, NT) * T2 + ((i & (T - 1)) << T_SHIFT) + (k & (T - 1));
+    return row_tile(i >> T_SHIFT, k >> T_SHIFT, NT) * Fmt<V>::ELEMS + (i & (T - 1)) * Fmt<V>::P + (k & (T - 1));
 }
 // Element (k, j) of a column-layout matrix, k <= j.
+template <typename V>
 __device__ __forceinline__ int64_t col_elem(int64_t k, int64_t j) {
-    return col_tile(k >> T_SHIFT, j >> T_SHIFT) * T2 + ((j & (T - 1)) << T_SHIFT) + (k & (T - 1));
+    return col_tile(k >> T_SHIFT, j >> T_SHIFT) * Fmt<V>::ELEMS + (j & (T - 1)) * Fmt<V>::P + (k & (T - 1));
 }
 
 template <typename V> struct Sentinel;
@@ -56,10 +70,17 @@ template <> struct MaxVal<int32_t> { static constexpr int value = INT32_MAX; };
 template <> struct MaxVal<int16_t> { static constexpr int value = INT16_MAX; };
 template <> struct MaxVal<uint8_t> { static constexpr int value = 255; };
 
-__device__ __forceinline__ int load_any(const void *p, int64_t idx, int dt) {
-    if (dt == DT_U8) return ((const uint8_t *)p)[idx];
-    if (dt == DT_I16) return ((const int16_t *)p)[idx];
-    return ((const int32_t *)p)[idx];
+// U(i, k) of a row-layout matrix / L(k, j) of a column-layout matrix whose
+// element type is known only at run time.
+__device__ __forceinline__ int load_row_any(const void *p, int64_t i, int64_t k, int64_t NT, int dt) {
+    if (dt == DT_U8) return ((const uint8_t *)p)[row_elem<uint8_t>(i, k, NT)];
+    if (dt == DT_I16) return ((const int16_t *)p)[row_elem<int16_t>(i, k, NT)];
+    return ((const int32_t *)p)[row_elem<int32_t>(i, k, NT)];
+}
+__device__ __forceinline__ int load_col_any(const void *p, int64_t k, int64_t j, int dt) {
+    if (dt == DT_U8) return ((const uint8_t *)p)[col_elem<uint8_t>(k, j)];
+    if (dt == DT_I16) return ((const int16_t *)p)[col_elem<int16_t>(k, j)];
+    return ((const int32_t *)p)[col_elem<int32_t>(k, j)];
 }
 
 __device__ __forceinline__ void set_error(int *err, int bits) {
@@ -120,5 +141,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
 }
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+// TMA bulk copy shared -> global (one bulk group); the caller fences the
+// generic-proxy writes first and waits for the reads before reusing smem.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 }  // namespace lcsg

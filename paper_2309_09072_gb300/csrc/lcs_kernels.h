@@ -53,7 +53,15 @@ struct MergeParams {
     int32_t full;          // 1: full-scan coarse level
     void *dense_out;       // output of LAYOUT_DENSE jobs (per call)
     int32_t *dense_K;      // optional dense argmax of LAYOUT_DENSE jobs (per call)
+    int32_t spill;         // 0: tiles whose band fits `cap`; 1: the others
+    int32_t cap_main;      // the main launch's cap (spill launches only)
 };
+
+// K-tiles per band for the main tile launch and the spill launch.
+int tile_cap_main(int in_dtype);
+int tile_cap_spill(int in_dtype, int out_dtype);
+// Main launch then spill launch of the tile kernel (2 kernel launches).
+cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStream_t st);
 
 // Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full
 // scans) then sigma0/2 .. 1 (windows bounded by the coarser level).

@@ -22,9 +22,11 @@
 //      (cp.async.bulk + mbarrier), then refines K from the four corners at
 //      stride 32, 16, .., 1 -- each level first the points with one new
 //      coordinate, then the points with two, every point bounded by already
-//      known neighbours -- and finally writes D (and K) out in the layout the
-//      consumer wants.  Tiles whose k-window exceeds the shared-memory band
-//      fall back to the same refinement reading global memory.
+//      known neighbours (a warp per grid row, a lane per point) -- and
+//      finally writes D out: a TMA bulk store of the tile for internal nodes,
+//      plain stores for a dense matrix.
+//      Tiles whose k-window exceeds the shared-memory band fall back to the
+//      same refinement reading global memory.
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
@@ -34,11 +36,11 @@ namespace lcsg {
 __device__ __forceinline__ int64_t grid_vertex(int64_t p, int64_t n) { return min(p * T, n); }
 
 // Warp-wide (value, k) reduction: largest value, smallest k among equals.
-__device__ __forceinline__ void warp_argmax(int &v, int64_t &k) {
+__device__ __forceinline__ void warp_argmax(int &v, int &k) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const int ov = __shfl_xor_sync(0xFFFFFFFFu, v, off);
-        const int64_t ok = __shfl_xor_sync(0xFFFFFFFFu, k, off);
+        const int ok = __shfl_xor_sync(0xFFFFFFFFu, k, off);
         if (ov > v || (ov == v && ok < k)) { v = ov; k = ok; }
     }
 }
@@ -72,28 +74,27 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
         if (!p.full && !newp && !newq) continue;
         const MergeJob jb = p.jobs[job];
         int32_t *kg = jb.kgrid;
-        const int64_t gi = grid_vertex(xp, n), gj = grid_vertex(xq, n);
-        int64_t lo = gi, hi = gj;
+        const int gi = (int)grid_vertex(xp, n), gj = (int)grid_vertex(xq, n);
+        int lo = gi, hi = gj;
         if (!p.full) {
             const int64_t td = newp ? t - 1 : t, tu = newp ? t + 1 : t;
             const int64_t ud = newq ? u - 1 : u, uu = newq ? u + 1 : u;
             const int64_t pd = min(td * sigma, P), pu = min(tu * sigma, P);
             const int64_t qd = min(ud * sigma, P), qu = min(uu * sigma, P);
-            lo = max(lo, (int64_t)kg[pd * (P + 1) + qd]);
-            hi = min(hi, (int64_t)kg[pu * (P + 1) + qu]);
+            lo = max(lo, kg[pd * (P + 1) + qd]);
+            hi = min(hi, kg[pu * (P + 1) + qu]);
         }
         const TIn *U = reinterpret_cast<const TIn *>(jb.U);
         const TIn *L = reinterpret_cast<const TIn *>(jb.L);
-        int best = INT32_MIN;
-        int64_t bk = INT64_MAX;
-        for (int64_t k = lo + lane; k <= hi; k += 32) {
-            const int v = (int)U[row_elem(gi, k, p.NT)] + (int)L[col_elem(k, gj)];
+        int best = INT32_MIN, bk = INT32_MAX;
+        for (int k = lo + lane; k <= hi; k += 32) {
+            const int v = (int)U[row_elem<TIn>(gi, k, p.NT)] + (int)L[col_elem<TIn>(k, gj)];
             if (v > best) { best = v; bk = k; }     // k increases: first max per lane
         }
         warp_argmax(best, bk);
         if (lane == 0) {
-            if (bk == INT64_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; }
-            kg[xp * (P + 1) + xq] = (int32_t)bk;
+            if (bk == INT32_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; }
+            kg[xp * (P + 1) + xq] = bk;
         }
     }
 }
@@ -116,28 +117,39 @@ cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
 // ------------------------------------------------------------------ tile
 constexpr int TP1 = T + 1;              // box points per side (with the far edge)
 constexpr int kTileThreads = 256;
+constexpr int kTileWarps = kTileThreads / 32;
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t align16c(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared-memory band buffer of one K-tile: T+1 rows at the stored pitch.
+template <typename V> struct Band {
+    static constexpr int BUF = (int)(align16c((size_t)TP1 * Fmt<V>::P * sizeof(V)) / sizeof(V));
+};
 
 struct TileSmem {
     size_t ks, ds, us, ls, total;
 };
-__host__ __device__ inline TileSmem tile_smem_layout(int in_sz, int out_sz, int cap) {
+__host__ __device__ inline TileSmem tile_smem_layout(int in_dt, int out_dt, int cap) {
     TileSmem s;
+    const size_t in_sz = dt_bytes(in_dt), out_sz = dt_bytes(out_dt);
+    const size_t buf = align16c((size_t)TP1 * tile_pitch(in_dt) * in_sz);
     size_t off = 16;                                  // mbarrier
-    s.ks = off; off = align16(off + (size_t)TP1 * TP1 * 4);
-    s.ds = off; off = align16(off + (size_t)T2 * out_sz);
-    s.us = off; off = align16(off + (size_t)cap * TP1 * T * in_sz);
-    s.ls = off; off = align16(off + (size_t)cap * TP1 * T * in_sz);
+    s.ks = off; off = align16c(off + (size_t)TP1 * TP1 * 4);
+    s.ds = off; off = align16c(off + (size_t)T * tile_pitch(out_dt) * out_sz);
+    s.us = off; off = align16c(off + (size_t)cap * buf);
+    s.ls = off; off = align16c(off + (size_t)cap * buf);
     s.total = off;
     return s;
 }
 
-static int dt_size(int dt) { return dt == DT_U8 ? 1 : (dt == DT_I16 ? 2 : 4); }
-
 size_t tile_smem_bytes(int in_dtype, int out_dtype, int cap) {
-    return tile_smem_layout(dt_size(in_dtype), dt_size(out_dtype), cap).total;
+    return tile_smem_layout(in_dtype, out_dtype, cap).total;
 }
+
+template <typename V> struct DtOf;
+template <> struct DtOf<uint8_t> { static constexpr int v = DT_U8; };
+template <> struct DtOf<int16_t> { static constexpr int v = DT_I16; };
+template <> struct DtOf<int32_t> { static constexpr int v = DT_I32; };
 
 // Number of s-grid points of [0, B] that are new at stride s (odd multiples
 // of s below B) and old (even multiples below B, plus B itself).
@@ -150,17 +162,174 @@ __device__ __forceinline__ void level_counts(int B, int s, int &nnew, int &nold,
 }
 __device__ __forceinline__ int old_coord(int q, int neven, int s, int B) { return q < neven ? 2 * q * s : B; }
 
+// Leftmost-argmax key of a candidate k: the value in the high half and the
+// complement of k's offset in the low half, so the largest key has the largest
+// value and, among equals, the smallest k (the tie rule of Algorithm 2).
+template <typename TIn> struct Key { using type = uint32_t; static constexpr int SHIFT = 16; };
+template <> struct Key<int32_t> { using type = uint64_t; static constexpr int SHIFT = 32; };
+
+template <typename K> __device__ __forceinline__ K warp_max_key(K v);
+template <> __device__ __forceinline__ uint32_t warp_max_key<uint32_t>(uint32_t v) {
+    return __reduce_max_sync(0xFFFFFFFFu, v);
+}
+template <> __device__ __forceinline__ uint64_t warp_max_key<uint64_t>(uint64_t v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v, off);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+// Operand access for the refinement: the staged shared-memory band, or the
+// tile-packed matrices in global memory (tiles whose window fits no band).
+template <typename TIn, bool SMEM> struct Operands;
+template <typename TIn> struct Operands<TIn, true> {
+    const TIn *Us, *Ls;
+    int kbase;
+    __device__ __forceinline__ int value(int x, int y, int k) const {
+        const int off = k - kbase;
+        const int e = (off >> T_SHIFT) * Band<TIn>::BUF + (off & (T - 1));
+        return (int)Us[x * Fmt<TIn>::P + e] + (int)Ls[y * Fmt<TIn>::P + e];
+    }
+};
+template <typename TIn> struct Operands<TIn, false> {
+    const TIn *Ug, *Lg;
+    int64_t NT;
+    int ia, ja;
+    __device__ __forceinline__ int value(int x, int y, int k) const {
+        return (int)Ug[row_elem<TIn>(ia + x, k, NT)] + (int)Lg[col_elem<TIn>(k, ja + y)];
+    }
+};
+
+// x / d for 0 <= x < 2^16 and 1 <= d <= 2^16 by one multiply-high
+// (d > 1: m = ceil(2^32 / d) makes the quotient exact in that range).
+struct FastDiv {
+    uint32_t d, m;
+    __device__ __forceinline__ explicit FastDiv(uint32_t dd)
+        : d(dd), m(dd > 1 ? (uint32_t)((0x100000000ull + dd - 1) / dd) : 0u) {}
+    __device__ __forceinline__ uint32_t div(uint32_t x) const { return d > 1 ? __umulhi(x, m) : x; }
+};
+
+// Coarse-to-fine refinement of K (and D) over the box [0, Bi] x [0, Bj] of a
+// tile whose four corners are known.  Each level s first resolves the points
+// with exactly one coordinate that is an odd multiple of s (bounded by the
+// two neighbours at distance s along that coordinate), then the points with
+// both (bounded by the four points just resolved).  Every lane resolves its
+// own point: the windows are short (about 1.7 candidates at s = 1, the level
+// that holds three quarters of the points), and a lane per point costs the
+// fewest instructions at every level.  Keys carry (value, -k) so a plain max
+// is the leftmost argmax.
+template <typename TIn, typename TOut, bool SMEM>
+__device__ __forceinline__ void refine_tile(const Operands<TIn, SMEM> op, int32_t *Ks, TOut *Ds, int layout,
+                                            int ia, int ja, int Bi, int Bj, int klo, int khi, int *err) {
+    using KeyT = typename Key<TIn>::type;
+    constexpr int SH = Key<TIn>::SHIFT;
+    constexpr KeyT LOW = (KeyT(1) << SH) - 1;
+    constexpr int PO = Fmt<TOut>::P;
+    int kb = 0;
+    if constexpr (SMEM) kb = op.kbase;
+    const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
+
+    // Resolve one point: scan [lo, hi], store K and (if owned) D.
+    auto point = [&](int x, int y, int lo, int hi) {
+        int best, bk;
+        bool found;
+        if constexpr (SMEM) {
+            lo = max(lo, klo);
+            hi = min(hi, khi);
+            KeyT key = 0;
+            int off = lo - kb;
+            int kk = off & (T - 1);
+            const int base = (off >> T_SHIFT) * Band<TIn>::BUF + kk;
+            const TIn *up = op.Us + x * Fmt<TIn>::P + base;
+            const TIn *lp = op.Ls + y * Fmt<TIn>::P + base;
+            for (int k = lo; k <= hi; ++k, ++off) {
+                const KeyT c = ((KeyT)(uint32_t)((int)*up + (int)*lp) << SH) | (LOW - (KeyT)off);
+                key = c > key ? c : key;
+                ++up;
+                ++lp;
+                if (++kk == T) { kk = 0; up += Band<TIn>::BUF - T; lp += Band<TIn>::BUF - T; }
+            }
+            found = key != 0;
+            best = (int)(key >> SH);
+            bk = found ? kb + (int)(LOW - (key & LOW)) : lo;
+        } else {
+            best = INT32_MIN;
+            bk = lo;
+            for (int k = lo; k <= hi; ++k) {
+                const int v = op.value(x, y, k);
+                if (v > best) { best = v; bk = k; }
+            }
+            found = lo <= hi;
+        }
+        if (!found) {                          // empty window: not a Monge input
+            set_error(err, ERR_BOUNDS);
+            best = 0;
+        }
+        if (best > MaxVal<TOut>::value) set_error(err, ERR_OVERFLOW);
+        Ks[x * TP1 + y] = bk;
+        if (x < T && y < T) Ds[x * ds_sx + y * ds_sy] = (TOut)best;
+    };
+
+    for (int s = T / 2; s >= 1; s >>= 1) {
+        int nnx, nox, nex, nny, noy, ney;
+        level_counts(Bi, s, nnx, nox, nex);
+        level_counts(Bj, s, nny, noy, ney);
+        const int cA = nnx * noy, cB = nox * nny, cC = nnx * nny;
+        const FastDiv dnoy((uint32_t)noy), dnny((uint32_t)nny);
+        // Sub-step 1: A = (x new, y old), then B = (x old, y new).
+        for (int idx = threadIdx.x; idx < cA + cB; idx += kTileThreads) {
+            int x, y, lo, hi;
+            if (idx < cA) {
+                const int qx = (int)dnoy.div((uint32_t)idx), qy = idx - qx * noy;
+                x = (2 * qx + 1) * s;
+                y = qy < ney ? 2 * qy * s : Bj;
+                lo = Ks[(x - s) * TP1 + y];
+                hi = Ks[min(x + s, Bi) * TP1 + y];
+            } else {
+                const int id2 = idx - cA;
+                const int qx = (int)dnny.div((uint32_t)id2), qy = id2 - qx * nny;
+                x = qx < nex ? 2 * qx * s : Bi;
+                y = (2 * qy + 1) * s;
+                lo = Ks[x * TP1 + (y - s)];
+                hi = Ks[x * TP1 + min(y + s, Bj)];
+            }
+            const int i = ia + x, j = ja + y;
+            if (i <= j) point(x, y, max(lo, i), min(hi, j));
+        }
+        __syncthreads();
+        // Sub-step 2: both coordinates new, bounded by the four neighbours.
+        for (int idx = threadIdx.x; idx < cC; idx += kTileThreads) {
+            const int qx = (int)dnny.div((uint32_t)idx), qy = idx - qx * nny;
+            const int x = (2 * qx + 1) * s, y = (2 * qy + 1) * s;
+            const int i = ia + x, j = ja + y;
+            if (i > j) continue;
+            const int xu = min(x + s, Bi), yu = min(y + s, Bj);
+            const int lo = max(max(Ks[x * TP1 + (y - s)], Ks[(x - s) * TP1 + y]), i);
+            const int hi = min(min(Ks[x * TP1 + yu], Ks[xu * TP1 + y]), j);
+            point(x, y, lo, hi);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
+    constexpr int PI = Fmt<TIn>::P, PO = Fmt<TOut>::P;
+    constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
+    constexpr int BUF = Band<TIn>::BUF;
     extern __shared__ __align__(128) unsigned char smem[];
-    const TileSmem L = tile_smem_layout((int)sizeof(TIn), (int)sizeof(TOut), p.cap);
+    const TileSmem SL = tile_smem_layout(DtOf<TIn>::v, DtOf<TOut>::v, p.cap);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int32_t *Ks = reinterpret_cast<int32_t *>(smem + L.ks);
-    TOut *Ds = reinterpret_cast<TOut *>(smem + L.ds);
-    TIn *Us = reinterpret_cast<TIn *>(smem + L.us);
-    TIn *Ls = reinterpret_cast<TIn *>(smem + L.ls);
+    int32_t *Ks = reinterpret_cast<int32_t *>(smem + SL.ks);
+    TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
+    TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
+    TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
+    __shared__ int s_ok;
 
-    const int64_t n = p.n, NT = p.NT, P = p.P;
+    const int64_t NT = p.NT, P = p.P;
+    const int n = (int)p.n;
     const MergeJob jb = p.jobs[blockIdx.y];
     // Tile index -> (I, J), row-major over the upper triangle of tiles.
     const int64_t tix = blockIdx.x;
@@ -174,65 +343,68 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
         I = lo;
     }
     const int64_t J = I + (tix - row_tile(I, I, NT));
-    const int64_t ia = I * T, ja = J * T;
-    const int Bi = (int)(min(ia + T, n) - ia), Bj = (int)(min(ja + T, n) - ja);
+    const int ia = (int)(I * T), ja = (int)(J * T);
+    const int Bi = min(ia + T, n) - ia, Bj = min(ja + T, n) - ja;
     const int64_t pa = I, pb = min(I + 1, P), qa = J, qb = min(J + 1, P);
-    auto kcorner = [&](int64_t pp, int64_t qq) -> int32_t {
+    auto kcorner = [&](int64_t pp, int64_t qq) -> int {
         const int64_t gi = grid_vertex(pp, n), gj = grid_vertex(qq, n);
-        return gi > gj ? (int32_t)gj : jb.kgrid[pp * (P + 1) + qq];
+        return gi > gj ? (int)gj : jb.kgrid[pp * (P + 1) + qq];
     };
-    int32_t klo = kcorner(pa, qa), khi = kcorner(pb, qb);
+    int klo = kcorner(pa, qa), khi = kcorner(pb, qb);
     // K(ia, ja) lies in [ia, ja] and K(ib, jb) in [ib, jb]; anything else
     // means the inputs are not DIST matrices: flag it and stage nothing.
     const bool corners_ok = klo >= ia && klo <= ja && khi >= ia + Bi && khi <= ja + Bj && klo <= khi;
     if (!corners_ok) {
         if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
-        klo = (int32_t)ia;
-        khi = (int32_t)(ja + Bj);
+        klo = ia;
+        khi = ja + Bj;
     }
-    const int64_t kt0 = klo >> T_SHIFT, kt1 = khi >> T_SHIFT;
-    const int nK = (int)(kt1 - kt0 + 1);
-    const int64_t kbase = kt0 * T;
+    const int kt0 = klo >> T_SHIFT, kt1 = khi >> T_SHIFT;
+    const int nK = kt1 - kt0 + 1;
+    const int kbase = kt0 * T;
+    // Two launches share the tiles: the main one (spill == 0) takes every
+    // tile whose band fits p.cap K-tiles, the spill one (spill == 1, larger
+    // band) the rest; a tile wider than even that reads global memory.
+    if (p.spill == 0 && corners_ok && nK > p.cap) return;
+    if (p.spill == 1 && !(corners_ok && nK > p.cap_main)) return;
     const bool in_smem = corners_ok && nK <= p.cap;
     const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
     const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
-    constexpr int TT = TP1 * T;         // elements per staged K-tile (T+1 rows)
 
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (in_smem && threadIdx.x == 0) {
-        // Byte count first, then the copies.
-        uint32_t bytes = 0;
-        const uint32_t tileB = (uint32_t)(T2 * sizeof(TIn)), rowB = (uint32_t)(T * sizeof(TIn));
-        const int64_t ltop = min(kt1, J);
-        bytes += (uint32_t)nK * tileB;                              // U band
-        const int64_t uextra = kt1 - max(kt0, I + 1) + 1;
-        if (Bi == T && uextra > 0) bytes += (uint32_t)uextra * rowB;
-        bytes += (uint32_t)(ltop - kt0 + 1) * tileB;                // L band
-        if (Bj == T) bytes += (uint32_t)(min(kt1, J + 1) - kt0 + 1) * rowB;
-        mbar_arrive_expect_tx(bar, bytes);
-        for (int64_t kt = kt0; kt <= kt1; ++kt) {
-            TIn *dst = Us + (kt - kt0) * TT;
-            bulk_g2s(dst, Ug + row_tile(I, kt, NT) * T2, tileB, bar);
-            if (Bi == T && kt >= I + 1) bulk_g2s(dst + T2, Ug + row_tile(I + 1, kt, NT) * T2, rowB, bar);
+        s_ok = 1;
+        if (in_smem) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+            const uint32_t tileB = (uint32_t)(EI * sizeof(TIn)), rowB = (uint32_t)(T * sizeof(TIn));
+            const int ltop = min(kt1, (int)J);
+            const int ufirst = max(kt0, (int)I + 1);
+            const int ltop2 = min(kt1, (int)J + 1);
+            uint32_t bytes = (uint32_t)nK * tileB + (uint32_t)(ltop - kt0 + 1) * tileB;
+            if (Bi == T && kt1 >= ufirst) bytes += (uint32_t)(kt1 - ufirst + 1) * rowB;
+            if (Bj == T) bytes += (uint32_t)(ltop2 - kt0 + 1) * rowB;
+            mbar_arrive_expect_tx(bar, bytes);
+            for (int kt = kt0; kt <= kt1; ++kt) {
+                TIn *dst = Us + (kt - kt0) * BUF;
+                bulk_g2s(dst, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
+                if (Bi == T && kt >= ufirst) bulk_g2s(dst + T * PI, Ug + row_tile(I + 1, kt, NT) * EI, rowB, bar);
+            }
+            for (int kt = kt0; kt <= ltop; ++kt)
+                bulk_g2s(Ls + (kt - kt0) * BUF, Lg + col_tile(kt, J) * EI, tileB, bar);
+            if (Bj == T)
+                for (int kt = kt0; kt <= ltop2; ++kt)
+                    bulk_g2s(Ls + (kt - kt0) * BUF + T * PI, Lg + col_tile(kt, J + 1) * EI, rowB, bar);
         }
-        for (int64_t kt = kt0; kt <= ltop; ++kt)
-            bulk_g2s(Ls + (kt - kt0) * TT, Lg + col_tile(kt, J) * T2, tileB, bar);
-        if (Bj == T)
-            for (int64_t kt = kt0; kt <= min(kt1, J + 1); ++kt)
-                bulk_g2s(Ls + (kt - kt0) * TT + T2, Lg + col_tile(kt, J + 1) * T2, rowB, bar);
     }
 
-    // Box initialisation: lower-triangle points hold j (k <= j bounds), the
-    // four corners come from the coarse grid, everything else is unknown.
-    for (int idx = threadIdx.x; idx < TP1 * TP1; idx += blockDim.x) {
-        const int x = idx / TP1, y = idx - x * TP1;
-        int32_t v = -1;
-        if (x <= Bi && y <= Bj && ia + x > ja + y) v = (int32_t)(ja + y);
-        Ks[idx] = v;
+    // Box initialisation (overlaps the copies).  Only a diagonal tile has
+    // lower-triangle points; they hold j, the k <= j bound.  Every other
+    // point is written before it is read.
+    if (I == J) {
+        for (int idx = threadIdx.x; idx < TP1 * TP1; idx += blockDim.x) {
+            const int x = idx / TP1, y = idx - x * TP1;
+            if (x > y) Ks[idx] = ja + y;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -240,139 +412,62 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
         Ks[Bj] = kcorner(pa, qb);
         Ks[Bi * TP1] = kcorner(pb, qa);
         Ks[Bi * TP1 + Bj] = khi;
+        // One thread waits for the band (bounded); the others park at the barrier.
+        if (in_smem && !mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+            set_error(p.err, ERR_TIMEOUT);
+            s_ok = 0;
+        }
     }
-    bool ok = true;
-    if (in_smem) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
-    if (!ok) set_error(p.err, ERR_TIMEOUT);
     __syncthreads();
-    // Every thread must agree on `ok`; a timed-out tile is skipped entirely.
-    ok = __syncthreads_and(ok);
-    if (!ok) return;
+    if (!s_ok) return;           // a timed-out tile is skipped by every thread
 
     const int layout = jb.d_layout;
-    auto ds_index = [&](int x, int y) -> int { return layout == LAYOUT_COL ? y * T + x : x * T + y; };
-
-    // Value of k for (x, y): SMEM band or global memory.
-    auto eval = [&](int x, int y, int64_t lo, int64_t hi, int &best, int64_t &bk) {
-        const int64_t i = ia + x, j = ja + y;
-        best = INT32_MIN;
-        if (in_smem) {
-            // A no-op for Monge inputs (every window lies in [klo, khi]); it
-            // keeps shared-memory reads inside the staged band for any input.
-            lo = max(lo, (int64_t)klo);
-            hi = min(hi, (int64_t)khi);
-        }
-        bk = lo;
-        if (lo > hi) { set_error(p.err, ERR_BOUNDS); return; }
-        if (in_smem) {
-            const TIn *ur = Us + x * T;
-            const TIn *lr = Ls + y * T;
-            for (int64_t k = lo; k <= hi; ++k) {
-                const int off = (int)(k - kbase);
-                const int e = (off >> T_SHIFT) * TT + (off & (T - 1));
-                const int v = (int)ur[e] + (int)lr[e];
-                if (v > best) { best = v; bk = k; }
-            }
-        } else {
-            for (int64_t k = lo; k <= hi; ++k) {
-                const int v = (int)Ug[row_elem(i, k, NT)] + (int)Lg[col_elem(k, j)];
-                if (v > best) { best = v; bk = k; }
-            }
-        }
-    };
-    auto finish = [&](int x, int y, int best, int64_t bk) {
-        if (best > MaxVal<TOut>::value) set_error(p.err, ERR_OVERFLOW);
-        Ks[x * TP1 + y] = (int32_t)bk;
-        if (x < T && y < T) Ds[ds_index(x, y)] = (TOut)best;
-    };
-
     // D at the corners that this tile owns (K known from the coarse grid).
     if (threadIdx.x < 4) {
         const int x = (threadIdx.x & 1) ? Bi : 0, y = (threadIdx.x & 2) ? Bj : 0;
         const bool dup = (threadIdx.x == 1 && Bi == 0) || (threadIdx.x == 2 && Bj == 0) ||
                          (threadIdx.x == 3 && (Bi == 0 || Bj == 0));
         if (!dup && x < T && y < T && ia + x <= ja + y) {
-            const int64_t k = Ks[x * TP1 + y];
-            int best;
-            int64_t bk;
-            eval(x, y, k, k, best, bk);
-            finish(x, y, best, bk);
+            const int k = Ks[x * TP1 + y];
+            int v;
+            if (in_smem) v = Operands<TIn, true>{Us, Ls, kbase}.value(x, y, k);
+            else v = Operands<TIn, false>{Ug, Lg, NT, ia, ja}.value(x, y, k);
+            Ds[layout == LAYOUT_COL ? y * PO + x : x * PO + y] = (TOut)v;
         }
     }
     __syncthreads();
-
-    for (int s = T / 2; s >= 1; s >>= 1) {
-        int nnx, nox, nex, nny, noy, ney;
-        level_counts(Bi, s, nnx, nox, nex);
-        level_counts(Bj, s, nny, noy, ney);
-        // Points with exactly one new coordinate.
-        const int cA = nnx * noy, cB = nox * nny;
-        for (int idx = threadIdx.x; idx < cA + cB; idx += blockDim.x) {
-            int x, y, xd, xu, yd, yu;
-            if (idx < cA) {
-                const int qx = idx / noy, qy = idx - qx * noy;
-                x = (2 * qx + 1) * s; y = old_coord(qy, ney, s, Bj);
-                xd = x - s; xu = min(x + s, Bi); yd = yu = y;
-            } else {
-                const int id2 = idx - cA;
-                const int qx = id2 / nny, qy = id2 - qx * nny;
-                x = old_coord(qx, nex, s, Bi); y = (2 * qy + 1) * s;
-                xd = xu = x; yd = y - s; yu = min(y + s, Bj);
-            }
-            const int64_t i = ia + x, j = ja + y;
-            if (i > j) continue;
-            const int64_t lo = max(i, (int64_t)Ks[xd * TP1 + yd]);
-            const int64_t hi = min(j, (int64_t)Ks[xu * TP1 + yu]);
-            int best;
-            int64_t bk;
-            eval(x, y, lo, hi, best, bk);
-            finish(x, y, best, bk);
-        }
-        __syncthreads();
-        // Points with two new coordinates, bounded by the four just computed.
-        const int cC = nnx * nny;
-        for (int idx = threadIdx.x; idx < cC; idx += blockDim.x) {
-            const int qx = idx / nny, qy = idx - qx * nny;
-            const int x = (2 * qx + 1) * s, y = (2 * qy + 1) * s;
-            const int64_t i = ia + x, j = ja + y;
-            if (i > j) continue;
-            const int xu = min(x + s, Bi), yu = min(y + s, Bj);
-            int64_t lo = max((int64_t)Ks[x * TP1 + (y - s)], (int64_t)Ks[(x - s) * TP1 + y]);
-            int64_t hi = min((int64_t)Ks[x * TP1 + yu], (int64_t)Ks[xu * TP1 + y]);
-            lo = max(lo, i);
-            hi = min(hi, j);
-            int best;
-            int64_t bk;
-            eval(x, y, lo, hi, best, bk);
-            finish(x, y, best, bk);
-        }
-        __syncthreads();
-    }
+    if (in_smem)
+        refine_tile<TIn, TOut, true>(Operands<TIn, true>{Us, Ls, kbase}, Ks, Ds, layout, ia, ja, Bi, Bj, klo, khi,
+                                     p.err);
+    else
+        refine_tile<TIn, TOut, false>(Operands<TIn, false>{Ug, Lg, NT, ia, ja}, Ks, Ds, layout, ia, ja, Bi, Bj,
+                                      klo, khi, p.err);
 
     // Output.
     if (layout == LAYOUT_DENSE) {
         TOut *out = reinterpret_cast<TOut *>(p.dense_out);
         int32_t *Kout = p.dense_K;
-        const int rows = (int)min((int64_t)T, n + 1 - ia), cols = (int)min((int64_t)T, n + 1 - ja);
+        const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
         for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
             const int x = idx >> T_SHIFT, y = idx & (T - 1);
             if (y >= cols) continue;
             const int64_t i = ia + x, j = ja + y;
-            out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * T + y];
+            out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * PO + y];
             if (Kout) Kout[i * p.ld + j] = (i > j) ? -1 : Ks[x * TP1 + y];
         }
-    } else {
+    } else if (threadIdx.x == 0) {
+        // TMA bulk store of the whole tile image (pitch included).
         const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
-        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<TOut *>(jb.D) + tile * T2);
-        const uint4 *src = reinterpret_cast<const uint4 *>(Ds);
-        constexpr int chunks = T2 * (int)sizeof(TOut) / 16;
-        for (int c = threadIdx.x; c < chunks; c += blockDim.x) dst[c] = src[c];
+        fence_proxy_async_smem();
+        bulk_s2g(reinterpret_cast<TOut *>(jb.D) + tile * EO, Ds, (uint32_t)(EO * sizeof(TOut)));
+        bulk_commit();
+        bulk_wait_read0();
     }
 }
 
 template <typename TIn, typename TOut>
 static cudaError_t launch_tile_t(const MergeParams &p, cudaStream_t st) {
-    const size_t smem = tile_smem_layout((int)sizeof(TIn), (int)sizeof(TOut), p.cap).total;
+    const size_t smem = tile_smem_layout(DtOf<TIn>::v, DtOf<TOut>::v, p.cap).total;
     auto kern = tile_kernel<TIn, TOut>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -395,12 +490,36 @@ cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaS
     return cudaErrorInvalidValue;
 }
 
+static size_t band_bytes(int in_dt) { return align16c((size_t)TP1 * tile_pitch(in_dt) * dt_bytes(in_dt)); }
+
+int tile_cap_main(int in_dtype) { return in_dtype == DT_I32 ? 2 : 4; }
+
+int tile_cap_spill(int in_dtype, int out_dtype) {
+    const size_t limit = 227 * 1024;
+    const size_t fixed = tile_smem_layout(in_dtype, out_dtype, 0).total;
+    const size_t cap = (limit - fixed) / (2 * band_bytes(in_dtype));
+    return (int)(cap > 32 ? 32 : cap);
+}
+
+cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStream_t st) {
+    const int cap_main = tile_cap_main(in_dtype);
+    p.spill = 0;
+    p.cap = cap_main;
+    p.cap_main = cap_main;
+    cudaError_t e = launch_tile(p, in_dtype, out_dtype, st);
+    if (e != cudaSuccess) return e;
+    p.spill = 1;
+    p.cap = tile_cap_spill(in_dtype, out_dtype);
+    return launch_tile(p, in_dtype, out_dtype, st);
+}
+
 // ------------------------------------------------------------------ pack
 // Dense (n+1) x ld -> tile-packed (one CTA per tile I <= J); the column
 // layout transposes each tile through shared memory.
 template <typename V>
 __global__ void __launch_bounds__(256) pack_kernel(const V *src, int64_t ld, int64_t n, int64_t NT,
                                                    V *dst, int layout) {
+    constexpr int P = Fmt<V>::P, E = Fmt<V>::ELEMS;
     __shared__ V tile[T][T + 1];
     const int64_t tix = blockIdx.x;
     int64_t lo = 0, hi = NT - 1;
@@ -415,15 +534,12 @@ __global__ void __launch_bounds__(256) pack_kernel(const V *src, int64_t ld, int
         tile[x][y] = (i <= n && j <= n) ? src[i * ld + j] : (V)0;
     }
     __syncthreads();
-    if (layout == LAYOUT_COL) {
-        V *d = dst + col_tile(I, J) * T2;
-        for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
-            const int y = idx >> T_SHIFT, x = idx & (T - 1);
-            d[idx] = tile[x][y];
-        }
-    } else {
-        V *d = dst + row_tile(I, J, NT) * T2;
-        for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) d[idx] = tile[idx >> T_SHIFT][idx & (T - 1)];
+    V *d = dst + ((layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT)) * E;
+    for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
+        const int r = idx / P, c = idx - r * P;
+        V v = (V)0;
+        if (c < T) v = (layout == LAYOUT_COL) ? tile[c][r] : tile[r][c];
+        d[idx] = v;
     }
 }
 

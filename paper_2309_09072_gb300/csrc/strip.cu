@@ -97,8 +97,9 @@ template <typename OutT>
 struct StagePitch {
     // Row-layout staging writes 32 lanes x 1 element at rows lane, lane+32 of
     // one column; a pitch of T + 4/sizeof(OutT) elements puts them in 32
-    // different banks.
-    static constexpr int value = T + 4 / (int)sizeof(OutT);
+    // different banks.  It is also the pitch of a stored tile, so a staged
+    // tile is written out as one contiguous image.
+    static constexpr int value = Fmt<OutT>::P;
 };
 
 constexpr int kStripWarps = 4;
@@ -215,14 +216,10 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
             }
         } else {
             const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, p.NT);
-            uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * T2);
-            constexpr int WPR = T * (int)sizeof(OutT) / 4;     // 32-bit words per tile row
-            constexpr int PB = P * (int)sizeof(OutT);          // staged row pitch in bytes
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(stage);
-            for (int w = lane; w < T * WPR; w += 32) {
-                const int r = w / WPR, cw = w - r * WPR;
-                dst[w] = *reinterpret_cast<const uint32_t *>(src + r * PB + cw * 4);
-            }
+            uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * Fmt<OutT>::ELEMS);
+            constexpr int WT = Fmt<OutT>::ELEMS * (int)sizeof(OutT) / 4;   // 32-bit words per tile
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(stage);
+            for (int w = lane; w < WT; w += 32) dst[w] = src[w];
         }
         __syncwarp();
     }

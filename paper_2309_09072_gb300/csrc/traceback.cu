@@ -32,8 +32,7 @@ __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
     int best = INT32_MIN;
     int64_t bk = INT64_MAX;
     for (int64_t k = i + threadIdx.x; k <= j; k += blockDim.x) {
-        const int v = load_any(mg.U, row_elem(i, k, p.NT), mg.in_dtype) +
-                      load_any(mg.L, col_elem(k, j), mg.in_dtype);
+        const int v = load_row_any(mg.U, i, k, p.NT, mg.in_dtype) + load_col_any(mg.L, k, j, mg.in_dtype);
         if (v > best) { best = v; bk = k; }
     }
 #pragma unroll
