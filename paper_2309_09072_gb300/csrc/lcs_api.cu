@@ -65,6 +65,7 @@ struct Group {               // merges of one level launched together
 struct Plan {
     int64_t m = -1, n = -1;
     int h = 0, words = 1, S = 0, levels = 0, root = -1;
+    bool dpx = false;        // every merge on the DPX (max,+) kernel, int16 nodes
     int64_t NT = 0, P = 0;
     int root_dt = DT_I32;    // dtype the root merge writes (caller's)
     std::vector<Node> nodes;
@@ -96,6 +97,7 @@ struct lcs_ctx {
     lcs_stats stats{};
     Plan plan;
     bool plan_uploaded = false;
+    bool auto_h = false;         // the current plan's h was chosen automatically
     int launches = 0;
     // profiling (lcs_set_profiling)
     bool profiling = false;
@@ -217,8 +219,13 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
     P.levels = level;
     P.root = cur[0];
     P.nodes[P.root].root = true;
+    // The DPX kernel adds int16 pairs: every operand value must stay at or
+    // below 16383 (a node's DIST is at most its row count).
+    P.dpx = true;
+    for (auto &mg : merges)
+        if (std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows) > 16383) P.dpx = false;
     for (auto &mg : merges) {
-        mg.in_dt = dt_for(std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows));
+        mg.in_dt = P.dpx ? (int)DT_I16 : dt_for(std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows));
         P.nodes[mg.u].dtype = mg.in_dt;
         P.nodes[mg.l].dtype = mg.in_dt;
     }
@@ -244,8 +251,8 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         off = align256(off + (size_t)tiles * tile_elems(nd.dtype) * dt_size(nd.dtype));
     }
     for (auto &mg : P.merges) {
-        mg.kgrid_off = off;
-        off = align256(off + (size_t)(P.P + 1) * (P.P + 1) * 4);
+        mg.kgrid_off = off;                       // kgrid then vgrid
+        off = align256(off + 2 * (size_t)(P.P + 1) * (P.P + 1) * 4);
     }
     P.off_strip_outs = off; off = align256(off + sizeof(StripOut) * P.S);
     P.off_jobs = off; off = align256(off + sizeof(MergeJob) * std::max<size_t>(1, P.merges.size()));
@@ -299,6 +306,7 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         j.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
         j.D = (mg.out == P.root) ? nullptr : reinterpret_cast<void *>(P.nodes[mg.out].off);
         j.kgrid = reinterpret_cast<int32_t *>(mg.kgrid_off);
+        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P + 1) * (P.P + 1) * 4);
         j.d_layout = (mg.out == P.root) ? LAYOUT_DENSE : P.nodes[mg.out].layout;
         P.h_jobs[q] = j;
     }
@@ -350,10 +358,31 @@ lcs_status ensure_io(lcs_ctx *ctx, size_t bytes) {
     return LCS_OK;
 }
 
+// Strip height when none is set: 128 rows (two 64-source chains per lane
+// with four 32-bit words each keep the SMs busy at n = 4096), doubled while
+// the retained tree would not fit the workspace budget.
+int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
+    int h = auto_strip_height(m, n);
+    while (h < 256 && m > h) {
+        const Plan q = build_plan(m, n, h, root_dt);
+        if (q.total + ctx->io_bytes <= ctx->budget) break;
+        h *= 2;
+    }
+    return h;
+}
+
 // Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
 lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
-    const int h = ctx->strip_h > 0 ? ctx->strip_h : auto_strip_height(m, n);
     Plan &P = ctx->plan;
+    int h = ctx->strip_h;
+    if (h <= 0) {
+        // Reuse the current plan's choice for the same shape.
+        h = (P.m == m && P.n == n && P.root_dt == root_dt && ctx->auto_h) ? P.h
+                                                                           : choose_strip_height(ctx, m, n, root_dt);
+        ctx->auto_h = true;
+    } else {
+        ctx->auto_h = false;
+    }
     if (!(P.m == m && P.n == n && P.h == h && P.root_dt == root_dt)) {
         // Kernels of an earlier call may still read the old descriptors.
         LCS_CK(ctx, cudaDeviceSynchronize());
@@ -373,6 +402,7 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
             j.L = reloc(base, (const char *)j.L);
             if (j.D) j.D = reloc(base, (char *)j.D);
             j.kgrid = reloc(base, j.kgrid);
+            j.vgrid = reloc(base, j.vgrid);
         }
         std::vector<TbMerge> tb = Q.h_tb;
         for (auto &t : tb) {
@@ -504,14 +534,19 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             mp.n = n; mp.NT = P.NT; mp.P = P.P; mp.ld = ld; mp.err = err;
             mp.dense_out = g.root ? dist : nullptr;
             mp.dense_K = nullptr;
+            mp.const_tiles = 1;
             mp.sigma = (int32_t)sigma0; mp.full = 1;
             LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
                 mp.sigma = (int32_t)sg; mp.full = 0;
                 LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             }
-            LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)), 0.0,
-                        launch_tile_pair(mp, g.in_dt, g.out_dt, st));
+            if (P.dpx)
+                LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                            0.0, launch_tile_dpx_pair(mp, g.out_dt, st));
+            else
+                LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                            0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, st));
             ctx->launches++;   // the pair is two kernel launches
             if (g.root)
                 LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
@@ -718,7 +753,7 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t NT = num_tiles_side(n), P = ceil_div(n, T);
     const size_t packed = align256((size_t)num_tiles_tri(NT) * tile_elems(dt) * dt_size(dt));
-    const size_t kg = align256((size_t)(P + 1) * (P + 1) * 4);
+    const size_t kg = align256(2 * (size_t)(P + 1) * (P + 1) * 4);   // kgrid + vgrid
     const size_t need = kHeaderBytes + 2 * packed + kg + align256(sizeof(MergeJob));
     if ((s = ensure_workspace(ctx, std::max(ctx->ws_bytes, kHeaderBytes))) != LCS_OK) return s;
     if ((s = ensure_io(ctx, need)) != LCS_OK) return s;
@@ -730,11 +765,13 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
     LCS_LAUNCHK(ctx, st, K_FILL, 0.0, 0.0, launch_pack(dist_l, dt, n, ld, Lp, LAYOUT_COL, st));
     MergeJob job{};
     job.U = Up; job.L = Lp; job.D = nullptr; job.kgrid = kgrid; job.d_layout = LAYOUT_DENSE;
+    job.vgrid = kgrid + (P + 1) * (P + 1);
     LCS_CK(ctx, cudaMemcpyAsync(jobd, &job, sizeof(job), cudaMemcpyHostToDevice, st));
     MergeParams mp{};
     mp.jobs = jobd; mp.njobs = 1;
     mp.n = n; mp.NT = NT; mp.P = P; mp.ld = ld; mp.err = err_word(ctx);
     mp.dense_out = dist_out; mp.dense_K = argmax_out;
+    mp.const_tiles = argmax_out ? 0 : 1;      // a constant tile has no argmax to report
     const int64_t sigma0 = coarse_sigma0(std::max<int64_t>(P, 1));
     mp.sigma = (int32_t)sigma0; mp.full = 1;
     LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, dt, st));

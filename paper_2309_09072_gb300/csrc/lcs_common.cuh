@@ -41,11 +41,13 @@ __host__ __device__ inline int64_t row_tile(int64_t I, int64_t J, int64_t NT) {
 __host__ __device__ inline int64_t col_tile(int64_t I, int64_t J) { return J * (J + 1) / 2 + I; }
 
 __host__ __device__ inline int dt_bytes(int dt) { return dt == 2 ? 1 : (dt == 1 ? 2 : 4); }
-// Stored tile: T rows of pitch T + 4/size elements.
-__host__ __device__ inline int tile_pitch(int dt) { return T + 4 / dt_bytes(dt); }
+// Stored tile: T rows of pitch T + 4 elements (int8/int16) or T + 1 (int32):
+// a few bytes per row so that rows fall into different shared-memory banks,
+// and, for int16, rows that start on 8-byte boundaries (64-bit loads).
+__host__ __device__ inline int tile_pitch(int dt) { return dt == 0 ? T + 1 : T + 4; }
 __host__ __device__ inline int64_t tile_elems(int dt) { return (int64_t)T * tile_pitch(dt); }
 template <typename V> struct Fmt {
-    static constexpr int P = T + 4 / (int)sizeof(V);
+    static constexpr int P = sizeof(V) == 4 ? T + 1 : T + 4;
     static constexpr int ELEMS = T * P;
 };
 

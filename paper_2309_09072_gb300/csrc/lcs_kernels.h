@@ -38,6 +38,7 @@ struct MergeJob {
     const void *L;       // lower operand, column layout
     void *D;             // output: packed (row/col layout) or dense (n+1) x ld
     int32_t *kgrid;      // (P+1) x (P+1) argmax on the T-grid (scratch)
+    int32_t *vgrid;      // (P+1) x (P+1) maximum (D itself) on the T-grid (scratch)
     int32_t d_layout;    // LAYOUT_ROW / LAYOUT_COL / LAYOUT_DENSE
     int32_t pad;
 };
@@ -55,6 +56,8 @@ struct MergeParams {
     int32_t *dense_K;      // optional dense argmax of LAYOUT_DENSE jobs (per call)
     int32_t spill;         // 0: tiles whose band fits `cap`; 1: the others
     int32_t cap_main;      // the main launch's cap (spill launches only)
+    int32_t const_tiles;   // 1: write tiles whose corner values agree as constants
+    int32_t pad;
 };
 
 // K-tiles per band for the main tile launch and the spill launch.
@@ -62,6 +65,9 @@ int tile_cap_main(int in_dtype);
 int tile_cap_spill(int in_dtype, int out_dtype);
 // Main launch then spill launch of the tile kernel (2 kernel launches).
 cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStream_t st);
+// DPX (max,+) tile launch for int16 operands whose values are at most 16383
+// (D only, no argmax), then the refinement kernel for the tiles it skips.
+cudaError_t launch_tile_dpx_pair(MergeParams p, int out_dtype, cudaStream_t st);
 
 // Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full
 // scans) then sigma0/2 .. 1 (windows bounded by the coarser level).

@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
         }
         warp_argmax(best, bk);
         if (lane == 0) {
-            if (bk == INT32_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; }
+            if (bk == INT32_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; best = 0; }
             kg[xp * (P + 1) + xq] = bk;
+            jb.vgrid[xp * (P + 1) + xq] = best;
         }
     }
 }
@@ -215,54 +216,30 @@ struct FastDiv {
 // tile whose four corners are known.  Each level s first resolves the points
 // with exactly one coordinate that is an odd multiple of s (bounded by the
 // two neighbours at distance s along that coordinate), then the points with
-// both (bounded by the four points just resolved).  Every lane resolves its
-// own point: the windows are short (about 1.7 candidates at s = 1, the level
-// that holds three quarters of the points), and a lane per point costs the
-// fewest instructions at every level.  Keys carry (value, -k) so a plain max
-// is the leftmost argmax.
+// both (bounded by the four points just resolved).  Windows are short on
+// average (about 1.9 candidates at s = 1, which holds three quarters of the
+// points) but heavy-tailed (the 99th percentile is near 40), and a warp runs
+// as long as its widest lane.  So a lane resolves its own point when the
+// window has at most kLaneWindow candidates; wider points go to a shared-
+// memory queue that whole warps then scan, lanes over k.  Keys carry
+// (value, -k) so a plain max is the leftmost argmax.
+constexpr int kLaneWindow = 16;
+constexpr int kQueueCap = 512;
+
 template <typename TIn, typename TOut, bool SMEM>
 __device__ __forceinline__ void refine_tile(const Operands<TIn, SMEM> op, int32_t *Ks, TOut *Ds, int layout,
-                                            int ia, int ja, int Bi, int Bj, int klo, int khi, int *err) {
+                                            int ia, int ja, int Bi, int Bj, int klo, int khi, int *err,
+                                            uint32_t *queue, int *qcount) {
     using KeyT = typename Key<TIn>::type;
     constexpr int SH = Key<TIn>::SHIFT;
     constexpr KeyT LOW = (KeyT(1) << SH) - 1;
     constexpr int PO = Fmt<TOut>::P;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int kb = 0;
     if constexpr (SMEM) kb = op.kbase;
     const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
 
-    // Resolve one point: scan [lo, hi], store K and (if owned) D.
-    auto point = [&](int x, int y, int lo, int hi) {
-        int best, bk;
-        bool found;
-        if constexpr (SMEM) {
-            lo = max(lo, klo);
-            hi = min(hi, khi);
-            KeyT key = 0;
-            int off = lo - kb;
-            int kk = off & (T - 1);
-            const int base = (off >> T_SHIFT) * Band<TIn>::BUF + kk;
-            const TIn *up = op.Us + x * Fmt<TIn>::P + base;
-            const TIn *lp = op.Ls + y * Fmt<TIn>::P + base;
-            for (int k = lo; k <= hi; ++k, ++off) {
-                const KeyT c = ((KeyT)(uint32_t)((int)*up + (int)*lp) << SH) | (LOW - (KeyT)off);
-                key = c > key ? c : key;
-                ++up;
-                ++lp;
-                if (++kk == T) { kk = 0; up += Band<TIn>::BUF - T; lp += Band<TIn>::BUF - T; }
-            }
-            found = key != 0;
-            best = (int)(key >> SH);
-            bk = found ? kb + (int)(LOW - (key & LOW)) : lo;
-        } else {
-            best = INT32_MIN;
-            bk = lo;
-            for (int k = lo; k <= hi; ++k) {
-                const int v = op.value(x, y, k);
-                if (v > best) { best = v; bk = k; }
-            }
-            found = lo <= hi;
-        }
+    auto store = [&](int x, int y, bool found, int best, int bk) {
         if (!found) {                          // empty window: not a Monge input
             set_error(err, ERR_BOUNDS);
             best = 0;
@@ -271,46 +248,130 @@ __device__ __forceinline__ void refine_tile(const Operands<TIn, SMEM> op, int32_
         Ks[x * TP1 + y] = bk;
         if (x < T && y < T) Ds[x * ds_sx + y * ds_sy] = (TOut)best;
     };
+    // One lane scans [lo, hi] (already clamped), left to right, one K-tile
+    // segment at a time.  `vcap` bounds D(x, y) from above (D is monotone,
+    // so a resolved neighbour above or to the right bounds it): the first k
+    // that reaches vcap is the leftmost maximiser and ends the scan.
+    auto lane_scan = [&](int x, int y, int lo, int hi, int vcap) {
+        if constexpr (SMEM) {
+            KeyT key = 0;
+            int off = lo - kb;
+            const int offhi = hi - kb;
+            const TIn *ur = op.Us + x * Fmt<TIn>::P;
+            const TIn *lr = op.Ls + y * Fmt<TIn>::P;
+            bool done = false;
+            while (off <= offhi && !done) {
+                const int seg_end = min(offhi, off | (T - 1));
+                const int e0 = (off >> T_SHIFT) * Band<TIn>::BUF + (off & (T - 1));
+                const TIn *up = ur + e0;
+                const TIn *lp = lr + e0;
+                for (; off <= seg_end; ++off, ++up, ++lp) {
+                    const int v = (int)*up + (int)*lp;
+                    const KeyT c = ((KeyT)(uint32_t)v << SH) | (LOW - (KeyT)off);
+                    key = c > key ? c : key;
+                    if (v >= vcap) { done = true; break; }
+                }
+            }
+            store(x, y, key != 0, (int)(key >> SH), key != 0 ? kb + (int)(LOW - (key & LOW)) : lo);
+        } else {
+            int best = INT32_MIN, bk = lo;
+            for (int k = lo; k <= hi; ++k) {
+                const int v = op.value(x, y, k);
+                if (v > best) { best = v; bk = k; }
+            }
+            store(x, y, lo <= hi, best, bk);
+        }
+    };
+    // D of a resolved owned point, or "no bound" for the far edges.
+    auto dval = [&](int x, int y) -> int {
+        return (x < T && y < T) ? (int)Ds[x * ds_sx + y * ds_sy] : INT32_MAX;
+    };
+    // Resolve or enqueue one point.
+    auto point = [&](int x, int y, int lo, int hi, int vcap, int *qc) {
+        if constexpr (SMEM) {
+            lo = max(lo, klo);
+            hi = min(hi, khi);
+            if (hi - lo >= kLaneWindow) {
+                const int slot = atomicAdd(qc, 1);
+                if (slot < kQueueCap) {
+                    // x, y < 128 and band offsets < 2^12 (cap <= 32 K-tiles).
+                    queue[2 * slot] = (uint32_t)x | ((uint32_t)y << 8);
+                    queue[2 * slot + 1] = (uint32_t)(lo - kb) | ((uint32_t)(hi - kb) << 16);
+                    return;
+                }
+            }
+        }
+        lane_scan(x, y, lo, hi, vcap);
+    };
+    // Whole warps drain the queue (lanes over k).
+    auto drain = [&](int count) {
+        if constexpr (SMEM) {
+            for (int q = warp; q < count; q += kTileWarps) {
+                const uint32_t w0 = queue[2 * q], w1 = queue[2 * q + 1];
+                const int x = (int)(w0 & 0xFF), y = (int)(w0 >> 8);
+                const int lo = kb + (int)(w1 & 0xFFFF), hi = kb + (int)(w1 >> 16);
+                KeyT key = 0;
+                for (int k = lo + lane; k <= hi; k += 32) {
+                    const KeyT c = ((KeyT)(uint32_t)op.value(x, y, k) << SH) | (LOW - (KeyT)(k - kb));
+                    key = c > key ? c : key;
+                }
+                key = warp_max_key<KeyT>(key);
+                if (lane == 0) store(x, y, key != 0, (int)(key >> SH), key != 0 ? kb + (int)(LOW - (key & LOW)) : lo);
+            }
+        }
+    };
 
+    int sub = 0;
     for (int s = T / 2; s >= 1; s >>= 1) {
         int nnx, nox, nex, nny, noy, ney;
         level_counts(Bi, s, nnx, nox, nex);
         level_counts(Bj, s, nny, noy, ney);
         const int cA = nnx * noy, cB = nox * nny, cC = nnx * nny;
         const FastDiv dnoy((uint32_t)noy), dnny((uint32_t)nny);
-        // Sub-step 1: A = (x new, y old), then B = (x old, y new).
-        for (int idx = threadIdx.x; idx < cA + cB; idx += kTileThreads) {
-            int x, y, lo, hi;
-            if (idx < cA) {
-                const int qx = (int)dnoy.div((uint32_t)idx), qy = idx - qx * noy;
-                x = (2 * qx + 1) * s;
-                y = qy < ney ? 2 * qy * s : Bj;
-                lo = Ks[(x - s) * TP1 + y];
-                hi = Ks[min(x + s, Bi) * TP1 + y];
-            } else {
-                const int id2 = idx - cA;
-                const int qx = (int)dnny.div((uint32_t)id2), qy = id2 - qx * nny;
-                x = qx < nex ? 2 * qx * s : Bi;
-                y = (2 * qy + 1) * s;
-                lo = Ks[x * TP1 + (y - s)];
-                hi = Ks[x * TP1 + min(y + s, Bj)];
+        for (int step = 0; step < 2; ++step, ++sub) {
+            // Three rotating counters: the next sub-step's counter was last
+            // read two sub-steps ago, and resetting it here is ordered
+            // before its next use by the barrier below.
+            int *qc = qcount + sub % 3;
+            if (threadIdx.x == 0) qcount[(sub + 1) % 3] = 0;
+            const int cnt = step == 0 ? cA + cB : cC;
+            for (int idx = threadIdx.x; idx < cnt; idx += kTileThreads) {
+                int x, y, lo, hi, vcap;
+                if (step == 1) {                 // both coordinates new
+                    const int qx = (int)dnny.div((uint32_t)idx), qy = idx - qx * nny;
+                    x = (2 * qx + 1) * s;
+                    y = (2 * qy + 1) * s;
+                    const int xu = min(x + s, Bi), yu = min(y + s, Bj);
+                    lo = max(Ks[x * TP1 + (y - s)], Ks[(x - s) * TP1 + y]);
+                    hi = min(Ks[x * TP1 + yu], Ks[xu * TP1 + y]);
+                    vcap = min(dval(x - s, y), dval(x, yu));
+                } else if (idx < cA) {           // x new, y old
+                    const int qx = (int)dnoy.div((uint32_t)idx), qy = idx - qx * noy;
+                    x = (2 * qx + 1) * s;
+                    y = qy < ney ? 2 * qy * s : Bj;
+                    lo = Ks[(x - s) * TP1 + y];
+                    hi = Ks[min(x + s, Bi) * TP1 + y];
+                    vcap = dval(x - s, y);
+                } else {                         // x old, y new
+                    const int id2 = idx - cA;
+                    const int qx = (int)dnny.div((uint32_t)id2), qy = id2 - qx * nny;
+                    x = qx < nex ? 2 * qx * s : Bi;
+                    y = (2 * qy + 1) * s;
+                    const int yu = min(y + s, Bj);
+                    lo = Ks[x * TP1 + (y - s)];
+                    hi = Ks[x * TP1 + yu];
+                    vcap = dval(x, yu);
+                }
+                const int i = ia + x, j = ja + y;
+                if (i <= j) point(x, y, max(lo, i), min(hi, j), vcap, qc);
             }
-            const int i = ia + x, j = ja + y;
-            if (i <= j) point(x, y, max(lo, i), min(hi, j));
+            __syncthreads();
+            const int queued = min(*qc, kQueueCap);
+            if (queued > 0) {
+                drain(queued);
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        // Sub-step 2: both coordinates new, bounded by the four neighbours.
-        for (int idx = threadIdx.x; idx < cC; idx += kTileThreads) {
-            const int qx = (int)dnny.div((uint32_t)idx), qy = idx - qx * nny;
-            const int x = (2 * qx + 1) * s, y = (2 * qy + 1) * s;
-            const int i = ia + x, j = ja + y;
-            if (i > j) continue;
-            const int xu = min(x + s, Bi), yu = min(y + s, Bj);
-            const int lo = max(max(Ks[x * TP1 + (y - s)], Ks[(x - s) * TP1 + y]), i);
-            const int hi = min(min(Ks[x * TP1 + yu], Ks[xu * TP1 + y]), j);
-            point(x, y, lo, hi);
-        }
-        __syncthreads();
     }
 }
 
@@ -327,6 +388,8 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
     __shared__ int s_ok;
+    __shared__ uint32_t s_queue[2 * kQueueCap];
+    __shared__ int s_qcount[3];
 
     const int64_t NT = p.NT, P = p.P;
     const int n = (int)p.n;
@@ -365,14 +428,53 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
     // Two launches share the tiles: the main one (spill == 0) takes every
     // tile whose band fits p.cap K-tiles, the spill one (spill == 1, larger
     // band) the rest; a tile wider than even that reads global memory.
+    // DIST is nonincreasing in i and nondecreasing in j (so is D), so the
+    // tile's smallest value sits at its bottom-left corner (ib, ja) and its
+    // largest at the top-right corner (ia, jb).  When the two agree (typical
+    // far from the diagonal in low merges, where both halves saturate) the
+    // tile is constant and needs neither staging nor refinement.
+    bool constant = false;
+    int cval = 0;
+    if (p.const_tiles && corners_ok && I != J) {
+        const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
+        constant = vmin == vmax;
+        cval = vmax;
+    }
+    if (constant) {
+        if (p.spill == 1) return;            // the main launch writes it
+        const int layout = jb.d_layout;
+        if (layout == LAYOUT_DENSE) {
+            TOut *out = reinterpret_cast<TOut *>(p.dense_out);
+            const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
+            for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
+                const int x = idx >> T_SHIFT, y = idx & (T - 1);
+                if (y < cols) out[(int64_t)(ia + x) * p.ld + ja + y] = (TOut)cval;
+            }
+        } else {
+            const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
+            TOut *dst = reinterpret_cast<TOut *>(jb.D) + tile * EO;
+            const TOut c = (TOut)cval;
+            // 16-byte stores of the replicated value (EO * size is a multiple of 16).
+            uint4 v;
+            TOut *vp = reinterpret_cast<TOut *>(&v);
+#pragma unroll
+            for (int t = 0; t < (int)(16 / sizeof(TOut)); ++t) vp[t] = c;
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (int c4 = threadIdx.x; c4 < (int)(EO * sizeof(TOut) / 16); c4 += blockDim.x) d4[c4] = v;
+        }
+        return;
+    }
     if (p.spill == 0 && corners_ok && nK > p.cap) return;
-    if (p.spill == 1 && !(corners_ok && nK > p.cap_main)) return;
+    if (p.spill == 1 && corners_ok && nK <= p.cap_main) return;
     const bool in_smem = corners_ok && nK <= p.cap;
     const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
     const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
 
     if (threadIdx.x == 0) {
         s_ok = 1;
+        s_qcount[0] = 0;
+        s_qcount[1] = 0;
+        s_qcount[2] = 0;
         if (in_smem) {
             mbar_init(bar, 1);
             fence_mbar_init();
@@ -438,10 +540,10 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
     __syncthreads();
     if (in_smem)
         refine_tile<TIn, TOut, true>(Operands<TIn, true>{Us, Ls, kbase}, Ks, Ds, layout, ia, ja, Bi, Bj, klo, khi,
-                                     p.err);
+                                     p.err, s_queue, s_qcount);
     else
         refine_tile<TIn, TOut, false>(Operands<TIn, false>{Ug, Lg, NT, ia, ja}, Ks, Ds, layout, ia, ja, Bi, Bj,
-                                      klo, khi, p.err);
+                                      klo, khi, p.err, s_queue, s_qcount);
 
     // Output.
     if (layout == LAYOUT_DENSE) {
@@ -490,12 +592,236 @@ cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaS
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------ DPX max-plus tile
+// For the merges of the tree the argmax is not needed (the traceback
+// recomputes it from the retained children), only D.  Within a tile every
+// K(i, j) lies in the band [K(ia, ja), K(ib, jb)] of the corners, so
+//     D(i, j) = max over k in the band, k in [i, j], of U(i, k) + L(k, j),
+// a (max,+) product of a 64 x W slice of U by a W x 64 slice of L.  It runs
+// on the DPX instruction __viaddmax_s16x2 (max(a + b, c) on two int16
+// lanes): the pair is taken along k, so a U row and an L column (a row of
+// the column-layout L) feed it straight from the tile-packed layout, and each
+// accumulator ends as max(low half, high half).  Entries with k < i (U) or
+// k > j (L) are set to -16384 in shared memory first; with every DIST value
+// at most 16383 such a sum stays negative.  Each of 128 threads owns an 8 x 4
+// block of outputs (rows ty + 8a, columns tx + 16b).
+constexpr int kDpxThreads = 128;
+constexpr int kDpxCap = 3;
+constexpr int16_t kNegInf16 = -16384;
+
+struct DpxSmem {
+    size_t ds, us, ls, total;
+};
+__host__ __device__ inline DpxSmem dpx_smem_layout(int out_dt, int cap) {
+    DpxSmem s;
+    const size_t tileb = (size_t)T * tile_pitch(DT_I16) * 2;   // 8704
+    size_t off = 16;
+    s.ds = off; off = align16c(off + (size_t)T * tile_pitch(out_dt) * dt_bytes(out_dt));
+    s.us = off; off = align16c(off + (size_t)cap * tileb);
+    s.ls = off; off = align16c(off + (size_t)cap * tileb);
+    s.total = off;
+    return s;
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
+    using TIn = int16_t;
+    constexpr int PI = Fmt<TIn>::P, PO = Fmt<TOut>::P;
+    constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const DpxSmem SL = dpx_smem_layout(DtOf<TOut>::v, p.cap);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
+    TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
+    TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
+    __shared__ int s_ok;
+
+    const int64_t NT = p.NT, P = p.P;
+    const int n = (int)p.n;
+    const MergeJob jb = p.jobs[blockIdx.y];
+    const int64_t tix = blockIdx.x;
+    int64_t I;
+    {
+        int64_t lo = 0, hi = NT - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (row_tile(mid, mid, NT) <= tix) lo = mid; else hi = mid - 1;
+        }
+        I = lo;
+    }
+    const int64_t J = I + (tix - row_tile(I, I, NT));
+    const int ia = (int)(I * T), ja = (int)(J * T);
+    const int Bi = min(ia + T, n) - ia, Bj = min(ja + T, n) - ja;
+    const int64_t pa = I, pb = min(I + 1, P), qa = J, qb = min(J + 1, P);
+    auto kcorner = [&](int64_t pp, int64_t qq) -> int {
+        const int64_t gi = grid_vertex(pp, n), gj = grid_vertex(qq, n);
+        return gi > gj ? (int)gj : jb.kgrid[pp * (P + 1) + qq];
+    };
+    const int klo = kcorner(pa, qa), khi = kcorner(pb, qb);
+    const bool corners_ok = klo >= ia && klo <= ja && khi >= ia + Bi && khi <= ja + Bj && klo <= khi;
+    const int layout = jb.d_layout;
+    // Constant tile (corner values agree): written here, nothing staged.
+    if (corners_ok && I != J) {
+        const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
+        if (vmin == vmax) {
+            if (layout == LAYOUT_DENSE) {
+                TOut *out = reinterpret_cast<TOut *>(p.dense_out);
+                const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
+                for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
+                    const int x = idx >> T_SHIFT, y = idx & (T - 1);
+                    if (y < cols) out[(int64_t)(ia + x) * p.ld + ja + y] = (TOut)vmax;
+                }
+            } else {
+                const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
+                uint4 v;
+                TOut *vp = reinterpret_cast<TOut *>(&v);
+#pragma unroll
+                for (int t = 0; t < (int)(16 / sizeof(TOut)); ++t) vp[t] = (TOut)vmax;
+                uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<TOut *>(jb.D) + tile * EO);
+                for (int c4 = threadIdx.x; c4 < (int)(EO * sizeof(TOut) / 16); c4 += blockDim.x) d4[c4] = v;
+            }
+            return;
+        }
+    }
+    const int kt0 = klo >> T_SHIFT;
+    const int ktop = min(khi >> T_SHIFT, (int)J);   // k <= ja + T - 1 suffices for owned columns
+    const int nK = ktop - kt0 + 1;
+    if (!corners_ok || nK > p.cap) return;          // the refinement (spill) launch takes it
+
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        const uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
+        mbar_arrive_expect_tx(bar, 2u * (uint32_t)nK * tileB);
+        const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
+        const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
+        for (int kt = kt0; kt <= ktop; ++kt) {
+            bulk_g2s(Us + (kt - kt0) * EI, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
+            bulk_g2s(Ls + (kt - kt0) * EI, Lg + col_tile(kt, J) * EI, tileB, bar);
+        }
+        if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+            set_error(p.err, ERR_TIMEOUT);
+            s_ok = 0;
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    // Mask k < i in U's diagonal tile, k > j in L's diagonal tile, and every
+    // k > n (stored tiles carry unspecified values past the last vertex).
+    // Masked + masked = -32768 still fits int16; a sentinel or stale value
+    // could wrap, so none is left in the band.
+    const int knT = n >> T_SHIFT, kn = n & (T - 1);
+    if (kt0 == (int)I || (knT >= kt0 && knT <= ktop)) {
+        for (int s2 = kt0; s2 <= ktop; ++s2) {
+            if (s2 != (int)I && s2 != knT) continue;
+            TIn *Ut = Us + (s2 - kt0) * EI;
+            for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
+                const int x = idx >> T_SHIFT, c = idx & (T - 1);
+                if ((s2 == (int)I && c < x) || (s2 == knT && c > kn)) Ut[x * PI + c] = kNegInf16;
+            }
+        }
+    }
+    for (int s2 = kt0; s2 <= ktop; ++s2) {
+        if (s2 != (int)J && s2 != knT) continue;
+        TIn *Lt = Ls + (s2 - kt0) * EI;
+        for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
+            const int y = idx >> T_SHIFT, c = idx & (T - 1);
+            if ((s2 == (int)J && c > y) || (s2 == knT && c > kn)) Lt[y * PI + c] = kNegInf16;
+        }
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    uint32_t acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
+    const int kbeg = max(klo & ~3, kt0 * T);
+    const int kend = min(khi, ja + T - 1) | 3;
+    for (int kt = kbeg >> T_SHIFT; kt <= (kend >> T_SHIFT); ++kt) {
+        const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
+        const TIn *Ub = Us + (kt - kt0) * EI + ty * PI;
+        const TIn *Lb = Ls + (kt - kt0) * EI + tx * PI;
+        for (int kk = lo; kk <= hi; kk += 4) {
+            uint2 u[8], l[4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kk);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) l[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kk);
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b] = __viaddmax_s16x2(u[a].x, l[b].x, acc[a][b]);
+                    acc[a][b] = __viaddmax_s16x2(u[a].y, l[b].y, acc[a][b]);
+                }
+        }
+    }
+    const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int x = ty + 8 * a, y = tx + 16 * b;
+            const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+            Ds[x * ds_sx + y * ds_sy] = (TOut)v;
+        }
+    __syncthreads();
+    if (layout == LAYOUT_DENSE) {
+        TOut *out = reinterpret_cast<TOut *>(p.dense_out);
+        const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
+        for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
+            const int x = idx >> T_SHIFT, y = idx & (T - 1);
+            if (y >= cols) continue;
+            const int64_t i = ia + x, j = ja + y;
+            out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * PO + y];
+        }
+    } else if (threadIdx.x == 0) {
+        const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
+        fence_proxy_async_smem();
+        bulk_s2g(reinterpret_cast<TOut *>(jb.D) + tile * EO, Ds, (uint32_t)(EO * sizeof(TOut)));
+        bulk_commit();
+        bulk_wait_read0();
+    }
+}
+
+template <typename TOut>
+static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
+    const size_t smem = dpx_smem_layout(DtOf<TOut>::v, p.cap).total;
+    auto kern = tile_dpx_kernel<TOut>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)num_tiles_tri(p.NT), (unsigned)p.njobs);
+    kern<<<grid, kDpxThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_dpx_pair(MergeParams p, int out_dtype, cudaStream_t st) {
+    p.spill = 0;
+    p.cap = kDpxCap;
+    cudaError_t e;
+    if (out_dtype == DT_I16) e = launch_dpx_t<int16_t>(p, st);
+    else if (out_dtype == DT_I32) e = launch_dpx_t<int32_t>(p, st);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    // Tiles the DPX launch skipped (band wider than kDpxCap K-tiles, or
+    // corners that are not a DIST's): the exact refinement kernel.
+    p.spill = 1;
+    p.cap_main = kDpxCap;
+    p.const_tiles = 1;
+    p.cap = tile_cap_spill(DT_I16, out_dtype);
+    return launch_tile(p, DT_I16, out_dtype, st);
+}
+
 static size_t band_bytes(int in_dt) { return align16c((size_t)TP1 * tile_pitch(in_dt) * dt_bytes(in_dt)); }
 
 int tile_cap_main(int in_dtype) { return in_dtype == DT_I32 ? 2 : 4; }
 
 int tile_cap_spill(int in_dtype, int out_dtype) {
-    const size_t limit = 227 * 1024;
+    // 227 KB per block, minus the kernel's static shared memory (the queue).
+    const size_t limit = 227 * 1024 - (2 * kQueueCap + 8) * 4 - 64;
     const size_t fixed = tile_smem_layout(in_dtype, out_dtype, 0).total;
     const size_t cap = (limit - fixed) / (2 * band_bytes(in_dtype));
     return (int)(cap > 32 ? 32 : cap);

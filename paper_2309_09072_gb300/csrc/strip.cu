@@ -19,6 +19,9 @@
 // shared-memory load per step).  Each finished T x T tile is staged in shared
 // memory (padded pitch, conflict-free) and written out with coalesced stores
 // in the layout its consumer wants (row or column tile-packed, or dense).
+// Once every source of a band has matched all rows of the strip, DIST stays
+// at h for the rest of the band's row, so the band's remaining tiles are
+// written as constants without further column steps.
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
@@ -96,13 +99,34 @@ __device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t
 template <typename OutT>
 struct StagePitch {
     // Row-layout staging writes 32 lanes x 1 element at rows lane, lane+32 of
-    // one column; a pitch of T + 4/sizeof(OutT) elements puts them in 32
-    // different banks.  It is also the pitch of a stored tile, so a staged
-    // tile is written out as one contiguous image.
+    // one column; the padded pitch of a stored tile (T + 4 or T + 1
+    // elements) spreads them over the banks, and a staged tile is then
+    // written out as one contiguous image.
     static constexpr int value = Fmt<OutT>::P;
 };
 
 constexpr int kStripWarps = 4;
+
+// Write one staged T x T tile: a contiguous image for the tile-packed
+// layouts, row by row for a dense matrix.
+template <typename OutT>
+__device__ __forceinline__ void write_tile(const StripParams &p, OutT *out, const OutT *stage, int layout, int64_t I,
+                                           int64_t J, int64_t i0, int64_t jb, int cmax, int lane) {
+    constexpr int P = Fmt<OutT>::P;
+    if (layout == LAYOUT_DENSE) {
+        const int64_t rows = min((int64_t)T, p.n + 1 - i0);
+        for (int r = 0; r < rows; ++r) {
+            OutT *dst = out + (i0 + r) * p.ld + jb;
+            for (int c = lane; c < cmax; c += 32) dst[c] = stage[r * P + c];
+        }
+    } else {
+        const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, p.NT);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * Fmt<OutT>::ELEMS);
+        constexpr int WT = Fmt<OutT>::ELEMS * (int)sizeof(OutT) / 4;   // 32-bit words per tile
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(stage);
+        for (int w = lane; w < WT; w += 32) dst[w] = src[w];
+    }
+}
 
 template <typename OutT, int W>
 __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) {
@@ -207,21 +231,20 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
             }
         }
         __syncwarp();
-        // Write the staged tile out.
-        if (layout == LAYOUT_DENSE) {
-            const int64_t rows = min((int64_t)T, n + 1 - i0);
-            for (int r = 0; r < rows; ++r) {
-                OutT *dst = out + (i0 + r) * p.ld + jb;
-                for (int c = lane; c < cmax; c += 32) dst[c] = stage[r * P + c];
-            }
-        } else {
-            const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, p.NT);
-            uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * Fmt<OutT>::ELEMS);
-            constexpr int WT = Fmt<OutT>::ELEMS * (int)sizeof(OutT) / 4;   // 32-bit words per tile
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(stage);
-            for (int w = lane; w < WT; w += 32) dst[w] = src[w];
-        }
+        write_tile<OutT>(p, out, stage, layout, I, J, i0, jb, cmax, lane);
         __syncwarp();
+        // Once every source of the band has matched all hs rows, DIST stays
+        // hs for the rest of the row: the remaining tiles are constant.
+        const bool saturated = __all_sync(0xFFFFFFFFu, (dA >= hs || i0 + rA > n) && (dB >= hs || i0 + rB > n));
+        if (saturated && J + 1 < p.NT) {
+            for (int e = lane; e < T * P; e += 32) stage[e] = (OutT)hs;
+            __syncwarp();
+            for (int64_t J2 = J + 1; J2 < p.NT; ++J2) {
+                const int64_t jb2 = J2 * T;
+                write_tile<OutT>(p, out, stage, layout, I, J2, i0, jb2, (int)min((int64_t)T, n + 1 - jb2), lane);
+            }
+            break;
+        }
     }
 }
 
