@@ -175,6 +175,26 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
                      lcs_dtype dtype, int64_t ld, void *dist_out, int32_t *argmax_out,
                      void *stream);
 
+/* lcs_merge without any device allocation, for callers that must not
+ * allocate device memory: code running under a framework that owns all
+ * device memory through its own pool, or a latency-critical loop in which a
+ * cudaMalloc would synchronise the device.  The paper has no counterpart; it
+ * is an interface convenience of this library.
+ * Same arguments and results as lcs_merge, but no context: every scratch
+ * byte comes from one static device array of 6 MiB that each GPU loading the
+ * library holds until the process exits, which limits n to 1024 (both
+ * dtypes; larger n returns EINVAL).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device
+ * current) and caches it, so make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents (each call clears what must start at zero); calls that
+ * overlap on the GPU race, so serialise them.  Synchronous: returns after
+ * the merge has finished on `stream`.
+ * Errors: EINVAL (n > 1024, bad layout, inputs that are not strip DIST
+ * matrices), ECUDA, ETIMEOUT, EOVERFLOW. */
+lcs_status lcs_merge_static(const void *dist_u, const void *dist_l, int64_t n, lcs_dtype dtype, int64_t ld,
+                            void *dist_out, int32_t *argmax_out, void *stream);
+
 /* Full DIST of the whole grid: dist(i, j) = LCS(a, b[i:j]).  dist: dense
  * (n+1) x ld in dtype (LCS_I16 needs m, n < 32768).  Asynchronous.
  * Errors: EINVAL, ENOMEM, ECUDA. */

@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_double)], st),
             "lcs_strip_dist": ([vp, vp, i32, vp, i64, st, vp, i64, vp], st),
             "lcs_merge": ([vp, vp, vp, i64, st, i64, vp, vp, vp], st),
+            "lcs_merge_static": ([vp, vp, i64, st, i64, vp, vp, vp], st),
             "lcs_dist": ([vp, vp, i64, vp, i64, st, vp, i64, vp], st),
             "lcs_length": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_traceback": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
@@ -220,6 +221,14 @@ def lcs_merge(ctx, dist_u, dist_l, dist_out, argmax_out=None, stream=None) -> No
     n = dist_u.shape[0] - 1
     _check(ctx, load().lcs_merge(ctx, _ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), _ld(dist_u),
                                  _ptr(dist_out), _ptr(argmax_out), _stream(stream)))
+
+
+def lcs_merge_static(dist_u, dist_l, dist_out, argmax_out=None, stream=None) -> None:
+    """lcs_merge with all scratch in the library's static device array (no
+    allocation, n <= 1024, synchronous)."""
+    n = dist_u.shape[0] - 1
+    _check(None, load().lcs_merge_static(_ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), _ld(dist_u),
+                                         _ptr(dist_out), _ptr(argmax_out), _stream(stream)))
 
 
 def lcs_dist(ctx, a, b, dist, stream=None) -> None:
