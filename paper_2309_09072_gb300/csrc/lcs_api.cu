@@ -541,13 +541,14 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 mp.sigma = (int32_t)sg; mp.full = 0;
                 LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             }
-            if (P.dpx)
+            if (P.dpx) {
                 LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, launch_tile_dpx_pair(mp, g.out_dt, st));
-            else
+                            0.0, launch_tile_dpx(mp, g.out_dt, st));
+            } else {
                 LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
                             0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, st));
-            ctx->launches++;   // the pair is two kernel launches
+                ctx->launches++;   // the pair is two kernel launches
+            }
             if (g.root)
                 LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
                                                   nullptr, st));

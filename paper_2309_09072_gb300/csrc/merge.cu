@@ -683,80 +683,87 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
             return;
         }
     }
-    const int kt0 = klo >> T_SHIFT;
-    const int ktop = min(khi >> T_SHIFT, (int)J);   // k <= ja + T - 1 suffices for owned columns
-    const int nK = ktop - kt0 + 1;
-    if (!corners_ok || nK > p.cap) return;          // the refinement (spill) launch takes it
-
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        mbar_init(bar, 1);
-        fence_mbar_init();
-        const uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
-        mbar_arrive_expect_tx(bar, 2u * (uint32_t)nK * tileB);
-        const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
-        const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
-        for (int kt = kt0; kt <= ktop; ++kt) {
-            bulk_g2s(Us + (kt - kt0) * EI, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
-            bulk_g2s(Ls + (kt - kt0) * EI, Lg + col_tile(kt, J) * EI, tileB, bar);
-        }
-        if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
-            set_error(p.err, ERR_TIMEOUT);
-            s_ok = 0;
-        }
+    // Band of k: [klo, khi] from the corners, k <= ja + T - 1 for owned
+    // columns.  Corners that are not a DIST's (invalid input) fall back to
+    // every k of the tile, [ia, ja + T - 1], and are flagged.
+    int kl = klo, kh = min(khi, ja + T - 1);
+    if (!corners_ok) {
+        if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
+        kl = ia;
+        kh = min(ja + T - 1, n);
     }
-    __syncthreads();
-    if (!s_ok) return;
-    // Mask k < i in U's diagonal tile, k > j in L's diagonal tile, and every
-    // k > n (stored tiles carry unspecified values past the last vertex).
-    // Masked + masked = -32768 still fits int16; a sentinel or stale value
-    // could wrap, so none is left in the band.
+    const int kt0 = kl >> T_SHIFT;
+    const int ktop = kh >> T_SHIFT;
+    const int kbeg = kl & ~3;
+    const int kend = kh | 3;
     const int knT = n >> T_SHIFT, kn = n & (T - 1);
-    if (kt0 == (int)I || (knT >= kt0 && knT <= ktop)) {
-        for (int s2 = kt0; s2 <= ktop; ++s2) {
-            if (s2 != (int)I && s2 != knT) continue;
-            TIn *Ut = Us + (s2 - kt0) * EI;
-            for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
-                const int x = idx >> T_SHIFT, c = idx & (T - 1);
-                if ((s2 == (int)I && c < x) || (s2 == knT && c > kn)) Ut[x * PI + c] = kNegInf16;
-            }
-        }
-    }
-    for (int s2 = kt0; s2 <= ktop; ++s2) {
-        if (s2 != (int)J && s2 != knT) continue;
-        TIn *Lt = Ls + (s2 - kt0) * EI;
-        for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
-            const int y = idx >> T_SHIFT, c = idx & (T - 1);
-            if ((s2 == (int)J && c > y) || (s2 == knT && c > kn)) Lt[y * PI + c] = kNegInf16;
-        }
-    }
-    __syncthreads();
-
+    const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
+    const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     uint32_t acc[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
-    const int kbeg = max(klo & ~3, kt0 * T);
-    const int kend = min(khi, ja + T - 1) | 3;
-    for (int kt = kbeg >> T_SHIFT; kt <= (kend >> T_SHIFT); ++kt) {
-        const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
-        const TIn *Ub = Us + (kt - kt0) * EI + ty * PI;
-        const TIn *Lb = Ls + (kt - kt0) * EI + tx * PI;
-        for (int kk = lo; kk <= hi; kk += 4) {
-            uint2 u[8], l[4];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    // The band streams through shared memory p.cap K-tiles at a time (one
+    // chunk for almost every tile); accumulators persist across chunks.
+    uint32_t phase = 0;
+    for (int c0 = kt0; c0 <= ktop; c0 += p.cap, phase ^= 1u) {
+        const int c1 = min(ktop, c0 + p.cap - 1);
+        __syncthreads();                      // previous chunk fully consumed
+        if (threadIdx.x == 0) {
+            s_ok = 1;
+            const uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
+            mbar_arrive_expect_tx(bar, 2u * (uint32_t)(c1 - c0 + 1) * tileB);
+            for (int kt = c0; kt <= c1; ++kt) {
+                bulk_g2s(Us + (kt - c0) * EI, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
+                bulk_g2s(Ls + (kt - c0) * EI, Lg + col_tile(kt, J) * EI, tileB, bar);
+            }
+            if (!mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+                set_error(p.err, ERR_TIMEOUT);
+                s_ok = 0;
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // Mask k < i in U's diagonal tile, k > j in L's diagonal tile, and
+        // every k > n (stored tiles carry unspecified values past the last
+        // vertex).  Masked + masked = -32768 still fits int16; a sentinel or
+        // stale value could wrap, so none is left in the band.
+        for (int kt = c0; kt <= c1; ++kt) {
+            const bool mu = kt == (int)I || kt == knT, ml = kt == (int)J || kt == knT;
+            if (!mu && !ml) continue;
+            TIn *Ut = Us + (kt - c0) * EI;
+            TIn *Lt = Ls + (kt - c0) * EI;
+            for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
+                const int r = idx >> T_SHIFT, c = idx & (T - 1);
+                if (mu && ((kt == (int)I && c < r) || (kt == knT && c > kn))) Ut[r * PI + c] = kNegInf16;
+                if (ml && ((kt == (int)J && c > r) || (kt == knT && c > kn))) Lt[r * PI + c] = kNegInf16;
+            }
+        }
+        __syncthreads();
+        for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
+            const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
+            const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
+            const TIn *Lb = Ls + (kt - c0) * EI + tx * PI;
+            for (int kk = lo; kk <= hi; kk += 4) {
+                uint2 u[8], l[4];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kk);
+                for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kk);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) l[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kk);
+                for (int b = 0; b < 4; ++b) l[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kk);
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+                for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b] = __viaddmax_s16x2(u[a].x, l[b].x, acc[a][b]);
-                    acc[a][b] = __viaddmax_s16x2(u[a].y, l[b].y, acc[a][b]);
-                }
+                    for (int b = 0; b < 4; ++b) {
+                        acc[a][b] = __viaddmax_s16x2(u[a].x, l[b].x, acc[a][b]);
+                        acc[a][b] = __viaddmax_s16x2(u[a].y, l[b].y, acc[a][b]);
+                    }
+            }
         }
     }
     const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
@@ -798,21 +805,12 @@ static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_dpx_pair(MergeParams p, int out_dtype, cudaStream_t st) {
+cudaError_t launch_tile_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
     p.spill = 0;
     p.cap = kDpxCap;
-    cudaError_t e;
-    if (out_dtype == DT_I16) e = launch_dpx_t<int16_t>(p, st);
-    else if (out_dtype == DT_I32) e = launch_dpx_t<int32_t>(p, st);
-    else return cudaErrorInvalidValue;
-    if (e != cudaSuccess) return e;
-    // Tiles the DPX launch skipped (band wider than kDpxCap K-tiles, or
-    // corners that are not a DIST's): the exact refinement kernel.
-    p.spill = 1;
-    p.cap_main = kDpxCap;
-    p.const_tiles = 1;
-    p.cap = tile_cap_spill(DT_I16, out_dtype);
-    return launch_tile(p, DT_I16, out_dtype, st);
+    if (out_dtype == DT_I16) return launch_dpx_t<int16_t>(p, st);
+    if (out_dtype == DT_I32) return launch_dpx_t<int32_t>(p, st);
+    return cudaErrorInvalidValue;
 }
 
 static size_t band_bytes(int in_dt) { return align16c((size_t)TP1 * tile_pitch(in_dt) * dt_bytes(in_dt)); }
