@@ -161,6 +161,24 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def recorded_traffic(kernel_src, summary):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since those counters were taken."""
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
+        fields = {}
+        for line in open(os.path.join(ROOT, "profiles", summary)):
+            if ":" in line and not line.startswith((" ", "|", "#")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_prefix") != sha:
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def roofline(profile, peaks, peaks_src, int_peak):
     """Dominant kernel (largest share of device time) against its bound."""
     if not profile:
@@ -177,8 +195,12 @@ def roofline(profile, peaks, peaks_src, int_peak):
                 "ms_per_launch": per_launch_ms, "launches": p["launches"]}
     achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
     peak = peaks["hbm_gbs"]
+    traffic = None
+    if kind == "merge_tile":
+        traffic = recorded_traffic("paper_2309_09072_gb300/csrc/merge.cu", "merge_tile_dpx_pair4096.md")
     return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": "hbm_gbs of %s" % peaks_src,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": "hbm_gbs of %s" % peaks_src,
+            "algorithmic_bytes_per_launch": p["bytes"] / p["launches"],
             "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"]}
 
 
