@@ -87,9 +87,23 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
         const TIn *U = reinterpret_cast<const TIn *>(jb.U);
         const TIn *L = reinterpret_cast<const TIn *>(jb.L);
         int best = INT32_MIN, bk = INT32_MAX;
-        for (int k = lo + lane; k <= hi; k += 32) {
-            const int v = (int)U[row_elem<TIn>(gi, k, p.NT)] + (int)L[col_elem<TIn>(k, gj)];
-            if (v > best) { best = v; bk = k; }     // k increases: first max per lane
+        // Walk the window one K-tile at a time: within a tile both U's row gi
+        // and L's column gj are contiguous, so each lane reads k = base + lane
+        // and base + 32 with the tile bases computed once per tile.
+        const int64_t Ib = gi >> T_SHIFT, Jb = gj >> T_SHIFT;
+        const int ro = (gi & (T - 1)) * Fmt<TIn>::P, co = (gj & (T - 1)) * Fmt<TIn>::P;
+#pragma unroll 8
+        for (int kt = lo >> T_SHIFT; kt <= (hi >> T_SHIFT); ++kt) {
+            const TIn *ub = U + row_tile(Ib, kt, p.NT) * Fmt<TIn>::ELEMS + ro;
+            const TIn *lb = L + col_tile(kt, Jb) * Fmt<TIn>::ELEMS + co;
+            const int k0 = kt * T;
+            const int ka = max(lo, k0), kz = min(hi, k0 + T - 1);
+            const int k1 = k0 + lane, k2 = k0 + 32 + lane;
+            const bool v1 = k1 >= ka && k1 <= kz, v2 = k2 >= ka && k2 <= kz;
+            const int x1 = v1 ? (int)ub[lane] + (int)lb[lane] : INT32_MIN;
+            const int x2 = v2 ? (int)ub[32 + lane] + (int)lb[32 + lane] : INT32_MIN;
+            if (x1 > best) { best = x1; bk = k1; }     // k increases: first max per lane
+            if (x2 > best) { best = x2; bk = k2; }
         }
         warp_argmax(best, bk);
         if (lane == 0) {
@@ -100,7 +114,54 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
     }
 }
 
+// The full-scan level: windows span up to n, so a whole CTA takes one grid
+// point (threads over k, then a block-wide leftmost argmax).
+template <typename TIn>
+__global__ void __launch_bounds__(256) coarse_full_kernel(MergeParams p) {
+    __shared__ int sv[8], sk[8];
+    const int64_t P = p.P, n = p.n, sigma = p.sigma;
+    const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);
+    const int64_t per_job = cnt * cnt;
+    const int job = (int)(blockIdx.x / per_job);
+    const int64_t rem = blockIdx.x - (int64_t)job * per_job;
+    const int64_t t = rem / cnt, u = rem - t * cnt;
+    const int64_t xp = min(t * sigma, P), xq = min(u * sigma, P);
+    if (xp > xq) return;
+    const MergeJob jb = p.jobs[job];
+    const TIn *U = reinterpret_cast<const TIn *>(jb.U);
+    const TIn *L = reinterpret_cast<const TIn *>(jb.L);
+    const int gi = (int)grid_vertex(xp, n), gj = (int)grid_vertex(xq, n);
+    int best = INT32_MIN, bk = INT32_MAX;
+#pragma unroll 4
+    for (int k = gi + (int)threadIdx.x; k <= gj; k += blockDim.x) {
+        const int v = (int)U[row_elem<TIn>(gi, k, p.NT)] + (int)L[col_elem<TIn>(k, gj)];
+        if (v > best) { best = v; bk = k; }     // k increases: first max per thread
+    }
+    warp_argmax(best, bk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] > best || (sv[w] == best && sk[w] < bk)) { best = sv[w]; bk = sk[w]; }
+        if (bk == INT32_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; best = 0; }
+        jb.kgrid[xp * (P + 1) + xq] = bk;
+        jb.vgrid[xp * (P + 1) + xq] = best;
+    }
+}
+
 cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
+    if (p.full) {
+        const int64_t cnt = p.P / p.sigma + 1 + ((p.P % p.sigma) ? 1 : 0);
+        const unsigned blocks = (unsigned)(cnt * cnt * p.njobs);
+        switch (in_dtype) {
+            case DT_U8: coarse_full_kernel<uint8_t><<<blocks, 256, 0, st>>>(p); break;
+            case DT_I16: coarse_full_kernel<int16_t><<<blocks, 256, 0, st>>>(p); break;
+            case DT_I32: coarse_full_kernel<int32_t><<<blocks, 256, 0, st>>>(p); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int64_t cnt = p.P / p.sigma + 2;
     const int64_t warps = cnt * cnt * p.njobs;
     int64_t blocks = ceil_div(warps, 8);

@@ -7,12 +7,12 @@
 //     c = min argmax_{i <= k <= j} U(i, k) + L(k, j)
 // (Sec. II-D: it is a by-product of the merge), and the two halves get the
 // sub-paths (i, c) and (c, j).  tb_level_kernel resolves one tree level per
-// launch, top down.  Inside a strip (leaf) the rows are resolved directly:
-// with F(r, c) = LCS(a_strip[0:r], b[i:c]) and B(r, c) = LCS(a_strip[r:h],
-// b[c:j]) from forward and backward bit-vector sweeps, v[r] = min{c : F + B =
-// DIST_strip(i, j)}; letter a_r is marked when the step between the cross
-// vertices of rows r-1 and r gains weight 1 (Sec. II-E).  The marked letters
-// of all strips, in row order, are the LCS.
+// launch, top down.  Inside a strip (leaf) the rows are resolved directly
+// from the forward bit vectors of F(r, c) = LCS(a_strip[0:r], b[i:c]) by a
+// backward walk that keeps every row's segment as far left as it can go (see
+// leaf_kernel); letter a_r is marked when the path enters row r by a weight-1
+// diagonal (Sec. II-E).  The marked letters of all strips, in row order, are
+// the LCS.
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
@@ -73,32 +73,13 @@ cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ leaves
-template <int W>
-__device__ __forceinline__ uint32_t add_chain(uint32_t (&s)[W], const uint32_t (&x)[W], const uint32_t (&y)[W]) {
-    // Multi-word add with carry out (portable form; the leaf sweep is short).
-    uint32_t c = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const uint64_t t = (uint64_t)x[w] + (uint64_t)y[w] + c;
-        s[w] = (uint32_t)t;
-        c = (uint32_t)(t >> 32);
-    }
-    return c;
-}
+constexpr int kLeafWarps = 2;
+constexpr int kLeafSmemCols = 1024;   // forward bit-vectors kept in shared memory
 
+// F(r, c) of a strip = zeros among the first r bits of its column vector V_c
+// (a zero bit marks a row where the DP steps up).
 template <int W>
-__device__ __forceinline__ void leaf_step(uint32_t (&V)[W], const uint32_t *M) {
-    uint32_t u[W], s[W], m[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) { m[w] = M[w]; u[w] = V[w] & m[w]; }
-    add_chain<W>(s, V, u);
-#pragma unroll
-    for (int w = 0; w < W; ++w) V[w] = s[w] | (V[w] & ~m[w]);
-}
-
-// Number of zero bits among bits [0, r) of the W-word vector at v.
-template <int W>
-__device__ __forceinline__ int zeros_below(const uint32_t (&v)[W], int r) {
+__device__ __forceinline__ int f_at(const uint32_t *v, int r) {
     int ones = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -109,45 +90,61 @@ __device__ __forceinline__ int zeros_below(const uint32_t (&v)[W], int r) {
     return r - ones;
 }
 
-constexpr int kLeafWarps = 2;
-
+// One warp per strip.  A forward bit-vector sweep from the strip's source i
+// stores V_c, c = i..j.  Then one lane walks back from the strip's sink
+// (h, j): left while F keeps its value (the heaviest path may run along the
+// row), else along the match diagonal if it is tight, else up.  Moving left
+// first keeps every row's segment as far left as it can go, so the row a
+// step leaves is left at its cross vertex v[r] = min{c : F(r,c)+B(r,c) =
+// DIST_strip(i, j)}: the leftmost heaviest path (Sec. II-C); a diagonal step
+// into row r marks letter a_r (Sec. II-E).
 template <int W>
 __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_warp_words = 2 * 256 * W + 2 * 260;
-    uint32_t *fm = reinterpret_cast<uint32_t *>(smem) + warp * per_warp_words;   // [256][W]
-    uint32_t *bm = fm + 256 * W;                                                  // [256][W]
-    int32_t *vv = reinterpret_cast<int32_t *>(bm + 256 * W);                     // [h+1]
-    int32_t *Fv = vv + 260;                                                       // [h+1]
+    const int per_warp_words = 256 * W + kLeafSmemCols * W;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem) + warp * per_warp_words;   // [256][W] match masks
+    uint32_t *vs = fm + 256 * W;                                                  // [kLeafSmemCols][W]
     const int s = blockIdx.x * kLeafWarps + warp;
     if (s >= p.S) return;
     const int64_t r0 = (int64_t)s * p.h;
     const int hs = (int)min((int64_t)p.h, p.m - r0);
     const int64_t i = p.pathI[s], j = p.pathJ[s];
 
-    for (int t = lane; t < 256 * W; t += 32) { fm[t] = 0u; bm[t] = 0u; }
+    for (int t = lane; t < 256 * W; t += 32) fm[t] = 0u;
     __syncwarp();
     for (int r = lane; r < hs; r += 32) {
         const uint8_t ch = p.a[r0 + r];
         atomicOr(&fm[ch * W + (r >> 5)], 1u << (r & 31));
-        const int rr = hs - 1 - r;                       // reversed row order
-        atomicOr(&bm[ch * W + (rr >> 5)], 1u << (rr & 31));
     }
     __syncwarp();
     if (i < 0 || j < i || j > p.n) {
         if (lane == 0) { set_error(p.err, ERR_BOUNDS); p.counts[s] = 0; }
         return;
     }
+    const int64_t ncol = j - i + 1;
+    const bool in_smem = ncol <= kLeafSmemCols;
+    uint32_t *vb = in_smem ? vs : p.vbuf + (i + s) * (int64_t)W;
 
-    // Forward sweep from source i; V_c stored for c = i..j.
-    uint32_t *vb = p.vbuf + (i + s) * (int64_t)W;
+    // Forward sweep (every lane computes V; lane w stores word w).
     uint32_t V[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
     if (lane < W) vb[lane] = 0xFFFFFFFFu;
     for (int64_t c = i + 1; c <= j; ++c) {
-        leaf_step<W>(V, fm + p.b[c - 1] * W);
+        const uint32_t *M = fm + p.b[c - 1] * W;
+        uint32_t u[W], sm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
+        uint32_t carry = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t t = (uint64_t)V[w] + (uint64_t)u[w] + carry;
+            sm[w] = (uint32_t)t;
+            carry = (uint32_t)(t >> 32);
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) V[w] = sm[w] | (V[w] & ~M[w]);
 #pragma unroll
         for (int w = 0; w < W; ++w)
             if (lane == w) vb[(c - i) * W + w] = V[w];
@@ -155,73 +152,54 @@ __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
     int ones = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) ones += __popc(V[w]);
-    const int Ltot = 32 * W - ones;               // padding bits stay 1
+    const int Ltot = 32 * W - ones;              // padding bits stay 1
     __syncwarp();
+    if (lane != 0) return;
 
-    // Backward sweep from sink j; rows r = lane + 32 q.
-    const int nq = (hs + 1 + 31) / 32;
-    uint32_t Wv[W];
+    // Backward walk (one lane).
+    int r = hs;
+    int64_t c = j;
+    uint32_t Vc[W], Vl[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) Wv[w] = 0xFFFFFFFFu;
-    int vloc[9];
+    for (int w = 0; w < W; ++w) Vc[w] = vb[(c - i) * W + w];
+    int pos = Ltot;
+    int fc = f_at<W>(Vc, r);
+    while (r > 0) {
+        if (c > i) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) vloc[q] = -1;
-    for (int64_t c = j; c >= i; --c) {
-        uint32_t Vc[W];
+            for (int w = 0; w < W; ++w) Vl[w] = vb[(c - 1 - i) * W + w];
+            if (f_at<W>(Vl, r) == fc) {           // left along row r
+                --c;
 #pragma unroll
-        for (int w = 0; w < W; ++w) Vc[w] = vb[(c - i) * W + w];
+                for (int w = 0; w < W; ++w) Vc[w] = Vl[w];
+                continue;
+            }
+            if (p.a[r0 + r - 1] == p.b[c - 1] && f_at<W>(Vl, r - 1) == fc - 1) {   // diagonal into row r
+                if (p.cross) p.cross[r0 + r] = (int32_t)c;
+                --pos;
+                if (pos >= 0) p.slots[(int64_t)s * p.h + pos] = p.a[r0 + r - 1];
+                --r;
+                --c;
+                --fc;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            if (q >= nq) break;
-            const int r = lane + 32 * q;
-            if (r > hs) continue;
-            const int F = zeros_below<W>(Vc, r);
-            const int B = zeros_below<W>(Wv, hs - r);
-            if (F + B == Ltot) vloc[q] = (int)c;
+                for (int w = 0; w < W; ++w) Vc[w] = Vl[w];
+                continue;
+            }
         }
-        if (c > i) leaf_step<W>(Wv, bm + p.b[c - 1] * W);
+        if (p.cross) p.cross[r0 + r] = (int32_t)c;   // up: row r is entered at c
+        --r;
+        fc = f_at<W>(Vc, r);
     }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        if (q >= nq) break;
-        const int r = lane + 32 * q;
-        if (r > hs) continue;
-        const int c = vloc[q];
-        vv[r] = c;
-        uint32_t Vc[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) Vc[w] = (c >= i) ? vb[(c - i) * W + w] : 0u;
-        Fv[r] = (c >= i) ? zeros_below<W>(Vc, r) : -1000000;
-    }
-    __syncwarp();
-    // Marks, in row order.
-    int base = 0;
-    for (int q = 0; q < nq; ++q) {
-        const int r = lane + 32 * q;
-        bool mark = false;
-        if (r >= 1 && r <= hs) mark = (Fv[r] - Fv[r - 1]) == 1;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, mark);
-        if (mark) {
-            const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            p.slots[(int64_t)s * p.h + pos] = p.a[r0 + r - 1];
-        }
-        base += __popc(bal);
-    }
-    if (lane == 0) {
-        p.counts[s] = base;
-        // Interior strips end at the next strip's cross vertex; the last strip
-        // ends at the sink (m, n), which need not be the cross vertex of row m.
-        if (base != Ltot || vv[0] != i || (s < p.S - 1 && vv[hs] != j)) set_error(p.err, ERR_BOUNDS);
-    }
-    if (p.cross) {
-        const bool last = (s == p.S - 1);
-        for (int r = lane; r < hs + (last ? 1 : 0); r += 32) p.cross[r0 + r] = vv[r];
-    }
+    // Row 0 of the strip is entered at its source i (the path may run along
+    // that row before stepping down, so the walk may stop right of i).
+    if (s == 0 && p.cross) p.cross[0] = (int32_t)i;
+    p.counts[s] = Ltot;
+    if (pos != 0) set_error(p.err, ERR_BOUNDS);
 }
 
 template <int W>
 static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
-    const size_t smem = (size_t)kLeafWarps * (2 * 256 * W + 2 * 260) * 4;
+    const size_t smem = (size_t)kLeafWarps * (256 * W + kLeafSmemCols * W) * 4;
     auto kern = leaf_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
