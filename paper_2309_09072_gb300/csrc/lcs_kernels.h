@@ -65,8 +65,9 @@ int tile_cap_main(int in_dtype);
 int tile_cap_spill(int in_dtype, int out_dtype);
 // Main launch then spill launch of the tile kernel (2 kernel launches).
 cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStream_t st);
-// DPX (max,+) tile launch for int16 operands whose values are at most 16383
-// (D only, no argmax); one launch covers every tile of every job.
+// DPX (max,+) merge of every tile of every job, for int16 operands whose
+// values are at most 16383 (D only, no argmax): one launch of persistent
+// CTAs after the coarse levels.
 cudaError_t launch_tile_dpx(MergeParams p, int out_dtype, cudaStream_t st);
 
 // Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full

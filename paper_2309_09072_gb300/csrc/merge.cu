@@ -27,6 +27,8 @@
 //      plain stores for a dense matrix.
 //      Tiles whose k-window exceeds the shared-memory band fall back to the
 //      same refinement reading global memory.
+#include <algorithm>
+
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
@@ -664,8 +666,14 @@ cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaS
 // the column-layout L) feed it straight from the tile-packed layout, and each
 // accumulator ends as max(low half, high half).  Entries with k < i (U) or
 // k > j (L) are set to -16384 in shared memory first; with every DIST value
-// at most 16383 such a sum stays negative.  Each of 128 threads owns an 8 x 4
-// block of outputs (rows ty + 8a, columns tx + 16b).
+// at most 16383 such a sum stays negative.  Each of 128 threads owns an
+// 8 x 4 block of outputs (rows ty + 8a, columns tx + 16b).
+// The CTAs are persistent: a CTA takes every G-th tile of the launch (all
+// jobs), warp 0 classifies 32 of them at a time (a lane per tile: corner
+// argmax and values, constant or not, band), and thread 0 issues the bulk
+// copies of the next staged tile's band as soon as the current tile's
+// product has read the shared-memory band, so they land while the current
+// tile is stored and the constant tiles in between are written.
 constexpr int kDpxThreads = 128;
 constexpr int kDpxCap = 3;
 constexpr int16_t kNegInf16 = -16384;
@@ -684,11 +692,21 @@ __host__ __device__ inline DpxSmem dpx_smem_layout(int out_dt, int cap) {
     return s;
 }
 
+// A tile of the launch as classified by warp 0.
+struct DpxMeta {
+    int32_t job, I, J;
+    int32_t kl, kh;            // band of k (inclusive)
+    int32_t cst;               // corner values agree: constant `val`
+    int32_t val;
+    int32_t valid;             // a tile of this CTA (else past the end)
+};
+
 template <typename TOut>
 __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     using TIn = int16_t;
     constexpr int PI = Fmt<TIn>::P, PO = Fmt<TOut>::P;
     constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
+    constexpr uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
     extern __shared__ __align__(128) unsigned char smem[];
     const DpxSmem SL = dpx_smem_layout(DtOf<TOut>::v, p.cap);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -696,162 +714,235 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
     __shared__ int s_ok;
+    __shared__ DpxMeta s_meta[32];
 
     const int64_t NT = p.NT, P = p.P;
     const int n = (int)p.n;
-    const MergeJob jb = p.jobs[blockIdx.y];
-    const int64_t tix = blockIdx.x;
-    int64_t I;
-    {
-        int64_t lo = 0, hi = NT - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (row_tile(mid, mid, NT) <= tix) lo = mid; else hi = mid - 1;
-        }
-        I = lo;
+    const int64_t tiles = num_tiles_tri(NT), total = tiles * p.njobs, G = gridDim.x;
+    const int knT = n >> T_SHIFT, kn = n & (T - 1);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
     }
-    const int64_t J = I + (tix - row_tile(I, I, NT));
-    const int ia = (int)(I * T), ja = (int)(J * T);
-    const int Bi = min(ia + T, n) - ia, Bj = min(ja + T, n) - ja;
-    const int64_t pa = I, pb = min(I + 1, P), qa = J, qb = min(J + 1, P);
-    auto kcorner = [&](int64_t pp, int64_t qq) -> int {
-        const int64_t gi = grid_vertex(pp, n), gj = grid_vertex(qq, n);
-        return gi > gj ? (int)gj : jb.kgrid[pp * (P + 1) + qq];
+    // Thread 0's view of the staging buffer: the K-tiles it holds (or is
+    // loading) and the barrier parity to wait for.
+    int st_tile = -1, st_c0 = -1;             // batch slot and first K-tile staged
+    uint32_t phase = 0;
+    bool store_pending = false;
+    auto issue = [&](const DpxMeta &m, int c0) {
+        const int c1 = min(m.kh >> T_SHIFT, c0 + p.cap - 1);
+        const MergeJob jb = p.jobs[m.job];
+        const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
+        const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
+        mbar_arrive_expect_tx(bar, 2u * (uint32_t)(c1 - c0 + 1) * tileB);
+        for (int kt = c0; kt <= c1; ++kt) {
+            bulk_g2s(Us + (kt - c0) * EI, Ug + row_tile(m.I, kt, NT) * EI, tileB, bar);
+            bulk_g2s(Ls + (kt - c0) * EI, Lg + col_tile(kt, m.J) * EI, tileB, bar);
+        }
     };
-    const int klo = kcorner(pa, qa), khi = kcorner(pb, qb);
-    const bool corners_ok = klo >= ia && klo <= ja && khi >= ia + Bi && khi <= ja + Bj && klo <= khi;
-    const int layout = jb.d_layout;
-    // Constant tile (corner values agree): written here, nothing staged.
-    if (corners_ok && I != J) {
-        const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
-        if (vmin == vmax) {
+
+    for (int64_t b0 = blockIdx.x; b0 < total; b0 += 32 * G) {
+        __syncthreads();                       // the previous batch's metadata is consumed
+        if (threadIdx.x < 32) {
+            // Lane l classifies tile b0 + l * G.
+            const int64_t g = b0 + lane * G;
+            DpxMeta m{};
+            if (g < total) {
+                m.valid = 1;
+                m.job = (int)(g / tiles);
+                const int64_t tix = g - m.job * tiles;
+                int64_t lo = 0, hi = NT - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if (row_tile(mid, mid, NT) <= tix) lo = mid; else hi = mid - 1;
+                }
+                m.I = (int)lo;
+                m.J = (int)(lo + (tix - row_tile(lo, lo, NT)));
+                const MergeJob jb = p.jobs[m.job];
+                const int ia = m.I * T, ja = m.J * T;
+                const int Bi = min(ia + T, n) - ia, Bj = min(ja + T, n) - ja;
+                const int64_t pa = m.I, pb = (m.I + 1 < P) ? m.I + 1 : P, qa = m.J, qb = (m.J + 1 < P) ? m.J + 1 : P;
+                auto kcorner = [&](int64_t pp, int64_t qq) -> int {
+                    const int64_t gi = grid_vertex(pp, n), gj = grid_vertex(qq, n);
+                    return gi > gj ? (int)gj : jb.kgrid[pp * (P + 1) + qq];
+                };
+                const int klo = kcorner(pa, qa), khi = kcorner(pb, qb);
+                const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
+                const bool ok = klo >= ia && klo <= ja && khi >= ia + Bi && khi <= ja + Bj && klo <= khi;
+                m.cst = (ok && m.I != m.J && vmin == vmax) ? 1 : 0;
+                m.val = vmax;
+                // Band [klo, khi], k <= ja + T - 1 for owned columns.  Corners
+                // that are not a DIST's (invalid input) fall back to every k
+                // of the tile, [ia, ja + T - 1], and are flagged.
+                m.kl = ok ? klo : ia;
+                m.kh = ok ? min(khi, ja + T - 1) : min(ja + T - 1, n);
+                if (!ok) set_error(p.err, ERR_BOUNDS);
+            }
+            s_meta[lane] = m;
+        }
+        __syncthreads();
+        for (int l = 0; l < 32; ++l) {
+            const DpxMeta m = s_meta[l];
+            if (!m.valid) break;
+            const MergeJob jb = p.jobs[m.job];
+            const int layout = jb.d_layout;
+            const int ia = m.I * T, ja = m.J * T;
+            if (m.cst) {
+                // Constant tile: written here, nothing staged.
+                if (layout == LAYOUT_DENSE) {
+                    TOut *out = reinterpret_cast<TOut *>(p.dense_out);
+                    const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
+                    for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
+                        const int x = idx >> T_SHIFT, y = idx & (T - 1);
+                        if (y < cols) out[(int64_t)(ia + x) * p.ld + ja + y] = (TOut)m.val;
+                    }
+                } else {
+                    const int64_t tile = (layout == LAYOUT_COL) ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
+                    uint4 v4;
+                    TOut *vp = reinterpret_cast<TOut *>(&v4);
+#pragma unroll
+                    for (int k = 0; k < (int)(16 / sizeof(TOut)); ++k) vp[k] = (TOut)m.val;
+                    uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<TOut *>(jb.D) + tile * EO);
+                    for (int c4 = threadIdx.x; c4 < (int)(EO * sizeof(TOut) / 16); c4 += blockDim.x) d4[c4] = v4;
+                }
+                continue;
+            }
+            const int kt0 = m.kl >> T_SHIFT, ktop = m.kh >> T_SHIFT;
+            const int kbeg = m.kl & ~3, kend = m.kh | 3;
+            uint32_t acc[8][4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
+            // The band streams through shared memory p.cap K-tiles at a time
+            // (one chunk for almost every tile); accumulators persist.
+            for (int c0 = kt0; c0 <= ktop; c0 += p.cap) {
+                const int c1 = min(ktop, c0 + p.cap - 1);
+                if (threadIdx.x == 0) {
+                    if (!(st_tile == l && st_c0 == c0)) issue(m, c0);   // not prefetched
+                    st_tile = -1;
+                    s_ok = 1;
+                    if (!mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+                        set_error(p.err, ERR_TIMEOUT);
+                        s_ok = 0;
+                    }
+                    phase ^= 1u;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                // Mask k < i in U's diagonal tile, k > j in L's diagonal tile,
+                // and every k > n (stored tiles carry unspecified values past
+                // the last vertex).  Masked + masked = -32768 still fits
+                // int16; a sentinel or stale value could wrap, so none is
+                // left in the band.
+                bool masked = false;
+                for (int kt = c0; kt <= c1; ++kt) {
+                    const bool mu = kt == m.I || kt == knT, ml = kt == m.J || kt == knT;
+                    if (!mu && !ml) continue;
+                    masked = true;
+                    TIn *Ut = Us + (kt - c0) * EI;
+                    TIn *Lt = Ls + (kt - c0) * EI;
+                    for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
+                        const int r = idx >> T_SHIFT, c = idx & (T - 1);
+                        if (mu && ((kt == m.I && c < r) || (kt == knT && c > kn))) Ut[r * PI + c] = kNegInf16;
+                        if (ml && ((kt == m.J && c > r) || (kt == knT && c > kn))) Lt[r * PI + c] = kNegInf16;
+                    }
+                }
+                if (masked) __syncthreads();
+                for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
+                    const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
+                    const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
+                    const TIn *Lb = Ls + (kt - c0) * EI + tx * PI;
+                    // Four k per step; the next step's operands load while
+                    // this step computes, and the two k pairs of a step go
+                    // through all 32 accumulators in turn, so that dependent
+                    // DPX instructions are 32 apart.
+                    uint2 u[8], lv[4];
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + lo);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) lv[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + lo);
+                    for (int kk = lo; kk <= hi; kk += 4) {
+                        const int kn = kk + 4 <= hi ? kk + 4 : kk;   // stays inside the staged tile
+                        uint2 un[8], ln[4];
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kn);
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kn);
+#pragma unroll
+                        for (int a = 0; a < 8; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = __viaddmax_s16x2(u[a].x, lv[b].x, acc[a][b]);
+#pragma unroll
+                        for (int a = 0; a < 8; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = __viaddmax_s16x2(u[a].y, lv[b].y, acc[a][b]);
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) u[a] = un[a];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) lv[b] = ln[b];
+                    }
+                }
+                if (threadIdx.x == 0 && c1 == ktop && store_pending) {
+                    bulk_wait_read0();          // the previous tile's store has read Ds
+                    store_pending = false;
+                }
+                __syncthreads();                // the band is read; Ds is free
+                if (threadIdx.x == 0) {
+                    if (c1 < ktop) {
+                        issue(m, c1 + 1);       // next chunk of this tile
+                        st_tile = l;
+                        st_c0 = c1 + 1;
+                    } else {
+                        // Prefetch the next staged tile of the batch.
+                        for (int l2 = l + 1; l2 < 32; ++l2) {
+                            const DpxMeta m2 = s_meta[l2];
+                            if (!m2.valid) break;
+                            if (m2.cst) continue;
+                            issue(m2, m2.kl >> T_SHIFT);
+                            st_tile = l2;
+                            st_c0 = m2.kl >> T_SHIFT;
+                            break;
+                        }
+                    }
+                }
+            }
+            const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int x = ty + 8 * a, y = tx + 16 * b;
+                    const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+                    Ds[x * ds_sx + y * ds_sy] = (TOut)v;
+                }
+            if (layout != LAYOUT_DENSE) fence_proxy_async_smem();
+            __syncthreads();
             if (layout == LAYOUT_DENSE) {
                 TOut *out = reinterpret_cast<TOut *>(p.dense_out);
                 const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
                 for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
                     const int x = idx >> T_SHIFT, y = idx & (T - 1);
-                    if (y < cols) out[(int64_t)(ia + x) * p.ld + ja + y] = (TOut)vmax;
+                    if (y >= cols) continue;
+                    const int64_t i = ia + x, j = ja + y;
+                    out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * PO + y];
                 }
-            } else {
-                const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
-                uint4 v;
-                TOut *vp = reinterpret_cast<TOut *>(&v);
-#pragma unroll
-                for (int t = 0; t < (int)(16 / sizeof(TOut)); ++t) vp[t] = (TOut)vmax;
-                uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<TOut *>(jb.D) + tile * EO);
-                for (int c4 = threadIdx.x; c4 < (int)(EO * sizeof(TOut) / 16); c4 += blockDim.x) d4[c4] = v;
+                __syncthreads();                // Ds read before the next tile writes it
+            } else if (threadIdx.x == 0) {
+                const int64_t tile = (layout == LAYOUT_COL) ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
+                bulk_s2g(reinterpret_cast<TOut *>(jb.D) + tile * EO, Ds, (uint32_t)(EO * sizeof(TOut)));
+                bulk_commit();
+                store_pending = true;
             }
-            return;
         }
     }
-    // Band of k: [klo, khi] from the corners, k <= ja + T - 1 for owned
-    // columns.  Corners that are not a DIST's (invalid input) fall back to
-    // every k of the tile, [ia, ja + T - 1], and are flagged.
-    int kl = klo, kh = min(khi, ja + T - 1);
-    if (!corners_ok) {
-        if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
-        kl = ia;
-        kh = min(ja + T - 1, n);
-    }
-    const int kt0 = kl >> T_SHIFT;
-    const int ktop = kh >> T_SHIFT;
-    const int kbeg = kl & ~3;
-    const int kend = kh | 3;
-    const int knT = n >> T_SHIFT, kn = n & (T - 1);
-    const TIn *Ug = reinterpret_cast<const TIn *>(jb.U);
-    const TIn *Lg = reinterpret_cast<const TIn *>(jb.L);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    uint32_t acc[8][4];
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    // The band streams through shared memory p.cap K-tiles at a time (one
-    // chunk for almost every tile); accumulators persist across chunks.
-    uint32_t phase = 0;
-    for (int c0 = kt0; c0 <= ktop; c0 += p.cap, phase ^= 1u) {
-        const int c1 = min(ktop, c0 + p.cap - 1);
-        __syncthreads();                      // previous chunk fully consumed
-        if (threadIdx.x == 0) {
-            s_ok = 1;
-            const uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
-            mbar_arrive_expect_tx(bar, 2u * (uint32_t)(c1 - c0 + 1) * tileB);
-            for (int kt = c0; kt <= c1; ++kt) {
-                bulk_g2s(Us + (kt - c0) * EI, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
-                bulk_g2s(Ls + (kt - c0) * EI, Lg + col_tile(kt, J) * EI, tileB, bar);
-            }
-            if (!mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
-                set_error(p.err, ERR_TIMEOUT);
-                s_ok = 0;
-            }
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        // Mask k < i in U's diagonal tile, k > j in L's diagonal tile, and
-        // every k > n (stored tiles carry unspecified values past the last
-        // vertex).  Masked + masked = -32768 still fits int16; a sentinel or
-        // stale value could wrap, so none is left in the band.
-        for (int kt = c0; kt <= c1; ++kt) {
-            const bool mu = kt == (int)I || kt == knT, ml = kt == (int)J || kt == knT;
-            if (!mu && !ml) continue;
-            TIn *Ut = Us + (kt - c0) * EI;
-            TIn *Lt = Ls + (kt - c0) * EI;
-            for (int idx = threadIdx.x; idx < T2; idx += blockDim.x) {
-                const int r = idx >> T_SHIFT, c = idx & (T - 1);
-                if (mu && ((kt == (int)I && c < r) || (kt == knT && c > kn))) Ut[r * PI + c] = kNegInf16;
-                if (ml && ((kt == (int)J && c > r) || (kt == knT && c > kn))) Lt[r * PI + c] = kNegInf16;
-            }
-        }
-        __syncthreads();
-        for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
-            const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
-            const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
-            const TIn *Lb = Ls + (kt - c0) * EI + tx * PI;
-            for (int kk = lo; kk <= hi; kk += 4) {
-                uint2 u[8], l[4];
-#pragma unroll
-                for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kk);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) l[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kk);
-#pragma unroll
-                for (int a = 0; a < 8; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        acc[a][b] = __viaddmax_s16x2(u[a].x, l[b].x, acc[a][b]);
-                        acc[a][b] = __viaddmax_s16x2(u[a].y, l[b].y, acc[a][b]);
-                    }
-            }
-        }
-    }
-    const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int x = ty + 8 * a, y = tx + 16 * b;
-            const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
-            Ds[x * ds_sx + y * ds_sy] = (TOut)v;
-        }
-    __syncthreads();
-    if (layout == LAYOUT_DENSE) {
-        TOut *out = reinterpret_cast<TOut *>(p.dense_out);
-        const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
-        for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
-            const int x = idx >> T_SHIFT, y = idx & (T - 1);
-            if (y >= cols) continue;
-            const int64_t i = ia + x, j = ja + y;
-            out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * PO + y];
-        }
-    } else if (threadIdx.x == 0) {
-        const int64_t tile = (layout == LAYOUT_COL) ? col_tile(I, J) : row_tile(I, J, NT);
-        fence_proxy_async_smem();
-        bulk_s2g(reinterpret_cast<TOut *>(jb.D) + tile * EO, Ds, (uint32_t)(EO * sizeof(TOut)));
-        bulk_commit();
-        bulk_wait_read0();
+        // A copy still in flight (prefetched past an error) lands before the
+        // CTA's shared memory goes away.
+        if (st_tile >= 0 && !mbar_wait_bounded(bar, phase, kWaitLimitNs)) set_error(p.err, ERR_TIMEOUT);
+        bulk_wait_all0();
     }
 }
 
@@ -861,8 +952,13 @@ static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
     auto kern = tile_dpx_kernel<TOut>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)num_tiles_tri(p.NT), (unsigned)p.njobs);
-    kern<<<grid, kDpxThreads, smem, st>>>(p);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDpxThreads, smem)) != cudaSuccess) return e;
+    const int64_t work = p.njobs * num_tiles_tri(p.NT);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
+    kern<<<(unsigned)grid, kDpxThreads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
