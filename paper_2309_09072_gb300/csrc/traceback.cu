@@ -76,6 +76,13 @@ cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st) {
 constexpr int kLeafWarps = 2;
 constexpr int kLeafSmemCols = 1024;   // forward bit-vectors kept in shared memory
 
+// Shared memory of one leaf warp: match masks, column vectors, the strip's
+// letters and b's segment.
+__host__ __device__ constexpr size_t leaf_warp_bytes(int W) {
+    return ((size_t)(256 * W + kLeafSmemCols * W) * 4 + (size_t)kLeafSmemCols * (W + 1) * 2 + 256 +
+            kLeafSmemCols + 15) / 16 * 16;
+}
+
 // F(r, c) of a strip = zeros among the first r bits of its column vector V_c
 // (a zero bit marks a row where the DP steps up).
 template <int W>
@@ -83,11 +90,108 @@ __device__ __forceinline__ int f_at(const uint32_t *v, int r) {
     int ones = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        const int lo = w * 32;
-        if (r >= lo + 32) ones += __popc(v[w]);
-        else if (r > lo) ones += __popc(v[w] & ((1u << (r - lo)) - 1u));
+        const int bits = min(max(r - 32 * w, 0), 32);          // of word w, the first `bits` rows
+        const uint32_t mask = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+        ones += __popc(v[w] & mask);
     }
     return r - ones;
+}
+
+// Forward sweep and backward walk of one strip whose path runs from (0, i)
+// to (hs, j): column vectors in vb and b's segment in sb (shared memory,
+// kSmem) or vb in the global scratch and b read from global memory.
+template <int W, bool kSmem>
+__device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0, int hs, int64_t i, int64_t j,
+                                          const uint32_t *fm, uint32_t *vb, uint16_t *pp, const uint8_t *sa,
+                                          const uint8_t *sb, int lane) {
+    auto bch = [&](int64_t c) -> uint8_t {
+        if constexpr (kSmem) return sb[c - 1 - i];
+        else return p.b[c - 1];
+    };
+    // Forward sweep (every lane computes V; lane w stores word w).
+    // With the column vectors in shared memory, lane w <= W also stores the
+    // ones in the words below w, so that the walk's F(r, c) is one table
+    // entry plus one masked popcount.
+    uint32_t V[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
+    if (lane < W) vb[lane] = 0xFFFFFFFFu;
+    if (kSmem && lane <= W) pp[lane] = (uint16_t)(32 * lane);
+    for (int64_t c = i + 1; c <= j; ++c) {
+        const uint32_t *M = fm + bch(c) * W;
+        uint32_t u[W], sm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
+        uint32_t carry = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t t = (uint64_t)V[w] + (uint64_t)u[w] + carry;
+            sm[w] = (uint32_t)t;
+            carry = (uint32_t)(t >> 32);
+        }
+        uint32_t mine = 0;                       // word `lane` of V, picked without branches
+        int below = 0;                           // ones in the words below `lane`
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            V[w] = sm[w] | (V[w] & ~M[w]);
+            mine = lane == w ? V[w] : mine;
+            below += w < lane ? __popc(V[w]) : 0;
+        }
+        if (lane < W) vb[(c - i) * W + lane] = mine;
+        if (kSmem && lane <= W) pp[(c - i) * (W + 1) + lane] = (uint16_t)below;
+    }
+    int ones = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) ones += __popc(V[w]);
+    const int Ltot = 32 * W - ones;              // padding bits stay 1
+    __syncwarp();
+    if (lane != 0) return;
+
+    // Backward walk (one lane).  F(r, c) = r minus the ones among the first
+    // r bits of V_c.
+    auto F = [&](int64_t c, int r) -> int {
+        const uint32_t *v = vb + (c - i) * W;
+        if constexpr (kSmem) {
+            const int w = r >> 5, bits = r & 31;
+            int ones = pp[(c - i) * (W + 1) + w];
+            if (bits) ones += __popc(v[w] & ((1u << bits) - 1u));
+            return r - ones;
+        } else {
+            uint32_t vv[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) vv[w] = v[w];
+            return f_at<W>(vv, r);
+        }
+    };
+    int r = hs;
+    int64_t c = j;
+    int pos = Ltot;
+    int fc = F(c, r);
+    while (r > 0) {
+        if (c > i) {
+            if (F(c - 1, r) == fc) {              // left along row r
+                --c;
+                continue;
+            }
+            if (sa[r - 1] == bch(c) && F(c - 1, r - 1) == fc - 1) {   // diagonal into row r
+                if (p.cross) p.cross[r0 + r] = (int32_t)c;
+                --pos;
+                if (pos >= 0) p.slots[(int64_t)s * p.h + pos] = sa[r - 1];
+                --r;
+                --c;
+                --fc;
+                continue;
+            }
+        }
+        if (p.cross) p.cross[r0 + r] = (int32_t)c;   // up: row r is entered at c
+        --r;
+        fc = F(c, r);
+    }
+    // Row 0 of the strip is entered at its source i (the path may run along
+    // that row before stepping down, so the walk may stop right of i).
+    if (s == 0 && p.cross) p.cross[0] = (int32_t)i;
+    p.counts[s] = Ltot;
+    if (pos != 0) set_error(p.err, ERR_BOUNDS);
 }
 
 // One warp per strip.  A forward bit-vector sweep from the strip's source i
@@ -102,9 +206,11 @@ template <int W>
 __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_warp_words = 256 * W + kLeafSmemCols * W;
-    uint32_t *fm = reinterpret_cast<uint32_t *>(smem) + warp * per_warp_words;   // [256][W] match masks
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + warp * leaf_warp_bytes(W));   // [256][W] match masks
     uint32_t *vs = fm + 256 * W;                                                  // [kLeafSmemCols][W]
+    uint16_t *pp = reinterpret_cast<uint16_t *>(vs + kLeafSmemCols * W);          // [kLeafSmemCols][W + 1]
+    uint8_t *sa = reinterpret_cast<uint8_t *>(pp + kLeafSmemCols * (W + 1));      // the strip's letters
+    uint8_t *sb = sa + 256;                                                       // b[i .. j - 1]
     const int s = blockIdx.x * kLeafWarps + warp;
     if (s >= p.S) return;
     const int64_t r0 = (int64_t)s * p.h;
@@ -115,6 +221,7 @@ __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
     __syncwarp();
     for (int r = lane; r < hs; r += 32) {
         const uint8_t ch = p.a[r0 + r];
+        sa[r] = ch;
         atomicOr(&fm[ch * W + (r >> 5)], 1u << (r & 31));
     }
     __syncwarp();
@@ -123,83 +230,21 @@ __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
         return;
     }
     const int64_t ncol = j - i + 1;
-    const bool in_smem = ncol <= kLeafSmemCols;
-    uint32_t *vb = in_smem ? vs : p.vbuf + (i + s) * (int64_t)W;
-
-    // Forward sweep (every lane computes V; lane w stores word w).
-    uint32_t V[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
-    if (lane < W) vb[lane] = 0xFFFFFFFFu;
-    for (int64_t c = i + 1; c <= j; ++c) {
-        const uint32_t *M = fm + p.b[c - 1] * W;
-        uint32_t u[W], sm[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
-        uint32_t carry = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint64_t t = (uint64_t)V[w] + (uint64_t)u[w] + carry;
-            sm[w] = (uint32_t)t;
-            carry = (uint32_t)(t >> 32);
-        }
-#pragma unroll
-        for (int w = 0; w < W; ++w) V[w] = sm[w] | (V[w] & ~M[w]);
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-            if (lane == w) vb[(c - i) * W + w] = V[w];
+    if (ncol <= kLeafSmemCols) {
+        // The letters the serial sweep and walk compare, and the column
+        // vectors, live in shared memory; a global access per step would
+        // dominate the walk.
+        for (int64_t t = lane; t < ncol - 1; t += 32) sb[t] = p.b[i + t];
+        __syncwarp();
+        leaf_path<W, true>(p, s, r0, hs, i, j, fm, vs, pp, sa, sb, lane);
+    } else {
+        leaf_path<W, false>(p, s, r0, hs, i, j, fm, p.vbuf + (i + s) * (int64_t)W, nullptr, sa, nullptr, lane);
     }
-    int ones = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) ones += __popc(V[w]);
-    const int Ltot = 32 * W - ones;              // padding bits stay 1
-    __syncwarp();
-    if (lane != 0) return;
-
-    // Backward walk (one lane).
-    int r = hs;
-    int64_t c = j;
-    uint32_t Vc[W], Vl[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) Vc[w] = vb[(c - i) * W + w];
-    int pos = Ltot;
-    int fc = f_at<W>(Vc, r);
-    while (r > 0) {
-        if (c > i) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) Vl[w] = vb[(c - 1 - i) * W + w];
-            if (f_at<W>(Vl, r) == fc) {           // left along row r
-                --c;
-#pragma unroll
-                for (int w = 0; w < W; ++w) Vc[w] = Vl[w];
-                continue;
-            }
-            if (p.a[r0 + r - 1] == p.b[c - 1] && f_at<W>(Vl, r - 1) == fc - 1) {   // diagonal into row r
-                if (p.cross) p.cross[r0 + r] = (int32_t)c;
-                --pos;
-                if (pos >= 0) p.slots[(int64_t)s * p.h + pos] = p.a[r0 + r - 1];
-                --r;
-                --c;
-                --fc;
-#pragma unroll
-                for (int w = 0; w < W; ++w) Vc[w] = Vl[w];
-                continue;
-            }
-        }
-        if (p.cross) p.cross[r0 + r] = (int32_t)c;   // up: row r is entered at c
-        --r;
-        fc = f_at<W>(Vc, r);
-    }
-    // Row 0 of the strip is entered at its source i (the path may run along
-    // that row before stepping down, so the walk may stop right of i).
-    if (s == 0 && p.cross) p.cross[0] = (int32_t)i;
-    p.counts[s] = Ltot;
-    if (pos != 0) set_error(p.err, ERR_BOUNDS);
 }
 
 template <int W>
 static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
-    const size_t smem = (size_t)kLeafWarps * (256 * W + kLeafSmemCols * W) * 4;
+    const size_t smem = (size_t)kLeafWarps * leaf_warp_bytes(W);
     auto kern = leaf_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
