@@ -13,12 +13,13 @@
 // add.cc/addc chain over 32-bit words, so 32..256 rows cost a handful of
 // INT32 instructions per (i, j).
 //
-// Work mapping: a warp owns one band of T = 64 sources (2 per lane, two
-// independent dependency chains) and sweeps j across the band's tiles J >= I
-// in lock step, so the match mask of column j is warp-uniform (one broadcast
-// shared-memory load per step).  Each finished T x T tile is staged in shared
-// memory (padded pitch, conflict-free) and written out with coalesced stores
-// in the layout its consumer wants (row or column tile-packed, or dense).
+// Work mapping: a pair of warps owns one band of T = 64 sources (one per
+// lane) and sweeps j across the band's tiles J >= I in lock step, so the
+// match mask of column j is warp-uniform (one broadcast shared-memory load
+// per step); a named barrier per pair orders the shared column masks and
+// staging tile.  Each finished T x T tile is staged in shared memory (padded
+// pitch, conflict-free) and written out with coalesced stores in the layout
+// its consumer wants (row or column tile-packed, or dense).
 // Once every source of a band has matched all rows of the strip, DIST stays
 // at h for the rest of the band's row, so the band's remaining tiles are
 // written as constants without further column steps.
@@ -106,16 +107,18 @@ struct StagePitch {
 };
 
 constexpr int kStripWarps = 4;
+constexpr int kStripBands = kStripWarps / 2;   // a pair of warps per band
 
-// Write one staged T x T tile: a contiguous image for the tile-packed
-// layouts, row by row for a dense matrix.
+// Write words [w0, w1) of one staged T x T tile: a contiguous image for the
+// tile-packed layouts, rows [w0, w1) for a dense matrix.
 template <typename OutT>
-__device__ __forceinline__ void write_tile(const StripParams &p, OutT *out, const OutT *stage, int layout, int64_t I,
-                                           int64_t J, int64_t i0, int64_t jb, int cmax, int lane) {
+__device__ __forceinline__ void write_tile_part(const StripParams &p, OutT *out, const OutT *stage, int layout,
+                                                int64_t I, int64_t J, int64_t i0, int64_t jb, int cmax, int lane,
+                                                int half) {
     constexpr int P = Fmt<OutT>::P;
     if (layout == LAYOUT_DENSE) {
         const int64_t rows = min((int64_t)T, p.n + 1 - i0);
-        for (int r = 0; r < rows; ++r) {
+        for (int r = half * (T / 2); r < min(rows, (int64_t)(half + 1) * (T / 2)); ++r) {
             OutT *dst = out + (i0 + r) * p.ld + jb;
             for (int c = lane; c < cmax; c += 32) dst[c] = stage[r * P + c];
         }
@@ -124,7 +127,7 @@ __device__ __forceinline__ void write_tile(const StripParams &p, OutT *out, cons
         uint32_t *dst = reinterpret_cast<uint32_t *>(out + tile * Fmt<OutT>::ELEMS);
         constexpr int WT = Fmt<OutT>::ELEMS * (int)sizeof(OutT) / 4;   // 32-bit words per tile
         const uint32_t *src = reinterpret_cast<const uint32_t *>(stage);
-        for (int w = lane; w < WT; w += 32) dst[w] = src[w];
+        for (int w = half * (WT / 2) + lane; w < (half ? WT : WT / 2); w += 32) dst[w] = src[w];
     }
 }
 
@@ -133,8 +136,9 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
     constexpr int P = StagePitch<OutT>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *masks = reinterpret_cast<uint32_t *>(smem);             // [256][W]
-    uint32_t *colm_all = masks + 256 * W;                             // [warps][T][W]
-    OutT *stage_all = reinterpret_cast<OutT *>(colm_all + kStripWarps * T * W);  // [warps][T][P]
+    uint32_t *colm_all = masks + 256 * W;                             // [bands][T][W]
+    OutT *stage_all = reinterpret_cast<OutT *>(colm_all + kStripBands * T * W);  // [bands][T][P]
+    __shared__ int s_sat[kStripBands][2];
 
     const int s = blockIdx.y;
     const int64_t r0 = (int64_t)s * p.h;
@@ -149,99 +153,89 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t I = (int64_t)p.band_first + (int64_t)blockIdx.x * kStripWarps + warp;
-    if (I >= p.NT) return;     // no block-wide barrier below this point
+    const int band = warp >> 1, half = warp & 1;
+    const int64_t I = (int64_t)p.band_first + (int64_t)blockIdx.x * kStripBands + band;
+    if (I >= p.NT) return;     // both warps of the pair; no block-wide barrier below this point
+    // The pair's named barrier (a constant id per branch keeps the CTA's
+    // hardware barrier count small).
+    auto pair_sync = [&]() {
+        if (band == 0) named_bar_sync(1, 64);
+        else named_bar_sync(2, 64);
+    };
 
-    uint32_t *colm = colm_all + warp * T * W;
-    OutT *stage = stage_all + warp * T * P;
+    uint32_t *colm = colm_all + band * T * W;
+    OutT *stage = stage_all + band * T * P;
     const int64_t n = p.n;
     const int64_t i0 = I * T;
     const int layout = p.dense ? (int)LAYOUT_DENSE : p.outs[s].layout;
     OutT *out = p.dense ? reinterpret_cast<OutT *>(p.dense) : reinterpret_cast<OutT *>(p.outs[s].base);
 
-    uint32_t VA[W], VB[W];
+    uint32_t V[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) { VA[w] = 0xFFFFFFFFu; VB[w] = 0xFFFFFFFFu; }
-    int dA = 0, dB = 0;
-    const int rA = lane, rB = lane + 32;       // rows of the staged tile
+    for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
+    int d = 0;
+    const int r = half * 32 + lane;            // this lane's source is i0 + r, row r of the staged tile
 
     for (int64_t J = I; J < p.NT; ++J) {
         const int64_t jb = J * T;
-        // Column masks of this tile: column c consumes letter b[jb + c - 1].
-        for (int c = lane; c < T; c += 32) {
+        // Column masks of this tile (each warp of the pair builds half):
+        // column c consumes letter b[jb + c - 1].
+        {
+            const int c = half * 32 + lane;
             const int64_t j = jb + c;
-            if (j >= 1 && j <= n) {
-                const uint8_t ch = p.b[j - 1];
+            const bool in = j >= 1 && j <= n;
+            const uint8_t ch = in ? p.b[j - 1] : 0;
 #pragma unroll
-                for (int w = 0; w < W; ++w) colm[c * W + w] = masks[ch * W + w];
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) colm[c * W + w] = 0u;
-            }
+            for (int w = 0; w < W; ++w) colm[c * W + w] = in ? masks[ch * W + w] : 0u;
         }
-        __syncwarp();
+        // The masks are complete, and the previous tile has left the stage.
+        pair_sync();
         const int cmax = (int)min((int64_t)T, n + 1 - jb);
         if (J == I) {
             // Diagonal tile: source i0+r starts at column r (DIST(i,i) = 0).
             for (int c = 0; c < cmax; ++c) {
                 uint32_t M[W];
 #pragma unroll
-                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
-                uint32_t MA[W], MB[W];
+                for (int w = 0; w < W; ++w) M[w] = (c > r) ? colm[c * W + w] : 0u;
+                d += (int)column_step<W>(V, M);
+                const OutT v = (c < r) ? Sentinel<OutT>::value : (OutT)d;
+                if (layout == LAYOUT_COL) stage[c * P + r] = v;
+                else stage[r * P + c] = v;
+            }
+        } else if (layout == LAYOUT_COL) {
+#pragma unroll 4
+            for (int c = 0; c < cmax; ++c) {
+                uint32_t M[W];
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    MA[w] = (c > rA) ? M[w] : 0u;
-                    MB[w] = (c > rB) ? M[w] : 0u;
-                }
-                dA += (int)column_step<W>(VA, MA);
-                dB += (int)column_step<W>(VB, MB);
-                const OutT vA = (c < rA) ? Sentinel<OutT>::value : (OutT)dA;
-                const OutT vB = (c < rB) ? Sentinel<OutT>::value : (OutT)dB;
-                if (layout == LAYOUT_COL) {
-                    stage[c * P + rA] = vA;
-                    stage[c * P + rB] = vB;
-                } else {
-                    stage[rA * P + c] = vA;
-                    stage[rB * P + c] = vB;
-                }
+                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
+                d += (int)column_step<W>(V, M);
+                stage[c * P + r] = (OutT)d;
             }
         } else {
-            if (layout == LAYOUT_COL) {
 #pragma unroll 4
-                for (int c = 0; c < cmax; ++c) {
-                    uint32_t M[W];
+            for (int c = 0; c < cmax; ++c) {
+                uint32_t M[W];
 #pragma unroll
-                    for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
-                    dA += (int)column_step<W>(VA, M);
-                    dB += (int)column_step<W>(VB, M);
-                    stage[c * P + rA] = (OutT)dA;
-                    stage[c * P + rB] = (OutT)dB;
-                }
-            } else {
-#pragma unroll 4
-                for (int c = 0; c < cmax; ++c) {
-                    uint32_t M[W];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
-                    dA += (int)column_step<W>(VA, M);
-                    dB += (int)column_step<W>(VB, M);
-                    stage[rA * P + c] = (OutT)dA;
-                    stage[rB * P + c] = (OutT)dB;
-                }
+                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
+                d += (int)column_step<W>(V, M);
+                stage[r * P + c] = (OutT)d;
             }
         }
-        __syncwarp();
-        write_tile<OutT>(p, out, stage, layout, I, J, i0, jb, cmax, lane);
-        __syncwarp();
         // Once every source of the band has matched all hs rows, DIST stays
         // hs for the rest of the row: the remaining tiles are constant.
-        const bool saturated = __all_sync(0xFFFFFFFFu, (dA >= hs || i0 + rA > n) && (dB >= hs || i0 + rB > n));
+        const bool sat_w = __all_sync(0xFFFFFFFFu, d >= hs || i0 + r > n);
+        if (lane == 0) s_sat[band][half] = sat_w ? 1 : 0;
+        pair_sync();         // the tile and both saturation flags are in
+        write_tile_part<OutT>(p, out, stage, layout, I, J, i0, jb, cmax, lane, half);
+        const bool saturated = s_sat[band][0] && s_sat[band][1];
         if (saturated && J + 1 < p.NT) {
-            for (int e = lane; e < T * P; e += 32) stage[e] = (OutT)hs;
-            __syncwarp();
+            pair_sync();     // both halves written before the stage is refilled
+            for (int e = half * 32 + lane; e < T * P; e += 64) stage[e] = (OutT)hs;
+            pair_sync();
             for (int64_t J2 = J + 1; J2 < p.NT; ++J2) {
                 const int64_t jb2 = J2 * T;
-                write_tile<OutT>(p, out, stage, layout, I, J2, i0, jb2, (int)min((int64_t)T, n + 1 - jb2), lane);
+                write_tile_part<OutT>(p, out, stage, layout, I, J2, i0, jb2, (int)min((int64_t)T, n + 1 - jb2), lane,
+                                      half);
             }
             break;
         }
@@ -251,13 +245,13 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
 template <typename OutT, int W>
 static cudaError_t launch_t(const StripParams &p, cudaStream_t st) {
     constexpr int P = StagePitch<OutT>::value;
-    const size_t smem = (size_t)256 * W * 4 + (size_t)kStripWarps * T * W * 4 +
-                        (size_t)kStripWarps * T * P * sizeof(OutT);
+    const size_t smem = (size_t)256 * W * 4 + (size_t)kStripBands * T * W * 4 +
+                        (size_t)kStripBands * T * P * sizeof(OutT);
     auto kern = strip_kernel<OutT, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t bands = p.NT - p.band_first;
-    dim3 grid((unsigned)ceil_div(bands, kStripWarps), (unsigned)p.S);
+    dim3 grid((unsigned)ceil_div(bands, kStripBands), (unsigned)p.S);
     kern<<<grid, kStripWarps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
