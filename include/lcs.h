@@ -238,6 +238,62 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,
                           void *dist_host, int64_t ld, uint8_t *lcs_host, int64_t cap,
                           int64_t *out_len_host, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent pairs.  The paper treats one pair; serving many
+ * pairs of uneven lengths is this library's extension of it.  A pair whose a
+ * has at most 2048 letters is one strip (all its rows fit one bit vector), so
+ * its tree has no merge level: the length is the strip's DIST(0, n) and one
+ * LCS the strip's leftmost heaviest path, computed for every such pair of a
+ * batch in one launch, a warp per pair.  Larger pairs go through the strip
+ * tree of lcs_solve, one after another, inside lcs_batch_submit.
+ * ---------------------------------------------------------------------- */
+#define LCS_WANT_STRING 1u
+
+typedef struct {
+    const uint8_t *a;       /* m device bytes (rows)                             */
+    int64_t m;
+    const uint8_t *b;       /* n device bytes (columns)                          */
+    int64_t n;
+    uint32_t flags;         /* LCS_WANT_STRING: also return one LCS              */
+} lcs_pair;
+
+typedef struct {
+    int64_t len;            /* LCS length                                        */
+    int64_t string_offset;  /* offset of the pair's LCS (len bytes) in the
+                               ticket's string buffer, -1 without LCS_WANT_STRING */
+    lcs_status status;      /* of this pair                                      */
+    double t_submit;        /* steady host clock (s) when the batch was submitted */
+    double t_done;          /* when the batch finished on the device, same clock  */
+} lcs_result;
+
+/* Queue `count` pairs (descriptors in host memory; the strings they point to
+ * stay valid until the batch is done) and return a ticket.  The batch runs
+ * asynchronously on a stream of its own; its device memory (descriptors,
+ * results, strings, and the column vectors of the pairs that want their LCS)
+ * counts against the context's budget.
+ * Errors: EINVAL (a NULL or negative argument), EAGAIN (the batch does not
+ * fit the budget next to what the context holds now: release finished
+ * batches or submit fewer pairs), ENOMEM, ECUDA. */
+lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs_host, int64_t count, uint64_t *ticket_host);
+
+/* Wait up to timeout_ms (0: just look, < 0: until done) for a batch.  When
+ * it is done, write min(count, cap) results in submission order and set
+ * *n_done_host = count; otherwise *n_done_host = 0.  The batch keeps its
+ * memory until lcs_batch_release.
+ * Errors: EINVAL (unknown ticket), EOVERFLOW (cap < count; the first cap are
+ * written), ECUDA. */
+lcs_status lcs_batch_poll(lcs_ctx *ctx, uint64_t ticket, lcs_result *results_host, int64_t cap,
+                          int64_t *n_done_host, int32_t timeout_ms);
+
+/* Copy the string buffer of a finished batch (the LCS of pair p at
+ * results[p].string_offset, results[p].len bytes) to `out` (host or device
+ * memory), waiting for the batch first; *bytes_host receives its size.
+ * Errors: EINVAL, EOVERFLOW (cap too small; nothing copied), ECUDA. */
+lcs_status lcs_batch_strings(lcs_ctx *ctx, uint64_t ticket, uint8_t *out, int64_t cap, int64_t *bytes_host);
+
+/* Wait for a batch and free its device memory.  Errors: EINVAL, ECUDA. */
+lcs_status lcs_batch_release(lcs_ctx *ctx, uint64_t ticket);
+
 #ifdef __cplusplus
 }
 #endif

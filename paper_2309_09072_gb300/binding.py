@@ -50,6 +50,29 @@ class lcs_kernel_profile(ctypes.Structure):
     ]
 
 
+LCS_WANT_STRING = 1
+
+
+class lcs_pair(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_void_p),
+        ("m", ctypes.c_int64),
+        ("b", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class lcs_result(ctypes.Structure):
+    _fields_ = [
+        ("len", ctypes.c_int64),
+        ("string_offset", ctypes.c_int64),
+        ("status", ctypes.c_int),
+        ("t_submit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
 KERNEL_KINDS = {0: "strip", 1: "coarse", 2: "merge_tile", 3: "traceback_level", 4: "traceback_leaf",
                 5: "compact", 6: "fill"}
 
@@ -98,6 +121,10 @@ def load(path: str = LIB_PATH):
             "lcs_traceback": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_solve": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, vp, vp, vp], st),
             "lcs_solve_host": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+            "lcs_batch_submit": ([vp, ctypes.POINTER(lcs_pair), i64, ctypes.POINTER(ctypes.c_uint64)], st),
+            "lcs_batch_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(lcs_result), i64, ctypes.POINTER(i64), i32], st),
+            "lcs_batch_strings": ([vp, ctypes.c_uint64, vp, i64, ctypes.POINTER(i64)], st),
+            "lcs_batch_release": ([vp, ctypes.c_uint64], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -270,6 +297,51 @@ def lcs_solve_host(ctx, a_host, b_host, dist_host=None, lcs_host=None, dtype=LCS
                                       dtype, _ptr(dist_host), ld, _ptr(lcs_host), cap, ctypes.byref(out),
                                       _stream(stream)))
     return out.value
+
+
+def lcs_batch_submit(ctx, pairs) -> int:
+    """Queue pairs [(a, b) or (a, b, want_string)] of device uint8 tensors;
+    returns the ticket.  The tensors must stay alive until the batch is done."""
+    arr = (lcs_pair * max(1, len(pairs)))()
+    for k, pr in enumerate(pairs):
+        a, b = pr[0], pr[1]
+        want = pr[2] if len(pr) > 2 else True
+        arr[k].a = a.data_ptr() if a.numel() else None
+        arr[k].m = int(a.numel())
+        arr[k].b = b.data_ptr() if b.numel() else None
+        arr[k].n = int(b.numel())
+        arr[k].flags = LCS_WANT_STRING if want else 0
+    ticket = ctypes.c_uint64()
+    _check(ctx, load().lcs_batch_submit(ctx, arr, len(pairs), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def lcs_batch_poll(ctx, ticket: int, count: int, timeout_ms: int = -1):
+    """List of result dicts when the batch is done within timeout_ms, else None."""
+    arr = (lcs_result * max(1, count))()
+    done = ctypes.c_int64()
+    _check(ctx, load().lcs_batch_poll(ctx, ticket, arr, count, ctypes.byref(done), int(timeout_ms)))
+    if done.value == 0 and count > 0:
+        return None
+    return [{"len": r.len, "string_offset": r.string_offset, "status": r.status, "t_submit": r.t_submit,
+             "t_done": r.t_done} for r in arr[:count]]
+
+
+def lcs_batch_strings(ctx, ticket: int) -> bytes:
+    """The batch's string buffer (each pair's LCS at its string_offset)."""
+    import torch
+    size = ctypes.c_int64()
+    probe = ctypes.c_int64()
+    status = load().lcs_batch_strings(ctx, ticket, None, 0, ctypes.byref(probe))
+    if status not in (LCS_OK, LCS_EOVERFLOW):
+        _check(ctx, status)
+    buf = torch.empty(max(1, probe.value), dtype=torch.uint8)
+    _check(ctx, load().lcs_batch_strings(ctx, ticket, _ptr(buf), int(probe.value), ctypes.byref(size)))
+    return bytes(buf[: size.value].numpy().tobytes())
+
+
+def lcs_batch_release(ctx, ticket: int) -> None:
+    _check(ctx, load().lcs_batch_release(ctx, ticket))
 
 
 class Context:

@@ -15,7 +15,10 @@
 // of the tree stays resident until the traceback has passed it; the context
 // workspace is sized from the plan and never exceeds the budget.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
+#include <map>
+#include <thread>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -82,6 +85,27 @@ struct Plan {
 
 constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int64) at 8
 
+// A submitted batch: its stream, completion events and one device block
+// holding descriptors, lengths, strings, column vectors and an error word.
+struct BatchTicket {
+    int64_t count = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    double t_submit = 0.0;
+    char *dev = nullptr;
+    size_t bytes = 0;
+    int64_t *d_lens = nullptr;
+    uint8_t *d_strings = nullptr;
+    int *d_err = nullptr;
+    int64_t strings_bytes = 0;
+    std::vector<int64_t> str_off;          // -1: no string wanted
+    std::vector<lcs_status> host_status;   // pairs solved at submit (the strip tree)
+};
+
+double steady_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 }  // namespace
 
 struct lcs_ctx {
@@ -104,6 +128,10 @@ struct lcs_ctx {
     struct Rec { int kind; cudaEvent_t e0, e1; double bytes, ops; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
+    // batches (lcs_batch_submit)
+    std::map<uint64_t, BatchTicket> tickets;
+    uint64_t next_ticket = 1;
+    size_t batch_bytes = 0;
 };
 
 namespace {
@@ -639,6 +667,13 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
+    for (auto &kv : ctx->tickets) {
+        BatchTicket &t = kv.second;
+        if (t.dev) cudaFree(t.dev);
+        if (t.ev_start) cudaEventDestroy(t.ev_start);
+        if (t.ev_done) cudaEventDestroy(t.ev_done);
+        if (t.stream) cudaStreamDestroy(t.stream);
+    }
     for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
@@ -868,6 +903,211 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
     if (lcs_host && len > 0) LCS_CK(ctx, cudaMemcpyAsync(lcs_host, ld_lcs, (size_t)len, cudaMemcpyDeviceToHost, st));
     LCS_CK(ctx, cudaStreamSynchronize(st));
     *out_len_host = len;
+    return LCS_OK;
+}
+
+// ----------------------------------------------------------------------------- batches
+lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, uint64_t *ticket_out) {
+    if (!ctx || !ticket_out || count < 0 || (count > 0 && !pairs)) return LCS_EINVAL;
+    *ticket_out = 0;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    const int64_t max_rows = batch_max_rows();
+    // Layout of the batch's device block.
+    int64_t n_small = 0, str_bytes = 0, scr_words = 0;
+    std::vector<int64_t> str_off(count, -1), scr_off(count, 0);
+    for (int64_t q = 0; q < count; ++q) {
+        const lcs_pair &pr = pairs[q];
+        if (pr.m < 0 || pr.n < 0 || (pr.m > 0 && !pr.a) || (pr.n > 0 && !pr.b))
+            return fail(ctx, LCS_EINVAL, "batch pair " + std::to_string(q) + ": bad string");
+        if (pr.m >= INT32_MAX / 2 || pr.n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "batch pair too long");
+        const bool want = (pr.flags & LCS_WANT_STRING) != 0;
+        if (want) {
+            str_off[q] = str_bytes;
+            str_bytes += std::min(pr.m, pr.n);
+        }
+        if (pr.m <= max_rows) {
+            ++n_small;
+            if (want && pr.m > 0 && pr.n > 0) {
+                scr_off[q] = scr_words;
+                scr_words += (pr.n + 1) * ((pr.m + 31) / 32);
+            }
+        }
+    }
+    const size_t o_pairs = 0;
+    const size_t o_order = align256(o_pairs + sizeof(BatchPair) * std::max<int64_t>(1, count));
+    const size_t o_lens = align256(o_order + sizeof(int32_t) * std::max<int64_t>(1, count));
+    const size_t o_err = align256(o_lens + sizeof(int64_t) * std::max<int64_t>(1, count));
+    const size_t o_str = align256(o_err + sizeof(int));
+    const size_t o_scr = align256(o_str + (size_t)std::max<int64_t>(1, str_bytes));
+    const size_t total = align256(o_scr + (size_t)scr_words * 4);
+    if (ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes + total > ctx->budget)
+        return fail(ctx, LCS_EAGAIN, "batch does not fit the budget now");
+
+    BatchTicket t;
+    t.count = count;
+    t.str_off = str_off;
+    t.strings_bytes = str_bytes;
+    t.host_status.assign(count, LCS_OK);
+    t.t_submit = steady_seconds();
+    auto cleanup = [&]() {
+        if (t.dev) cudaFree(t.dev);
+        if (t.ev_start) cudaEventDestroy(t.ev_start);
+        if (t.ev_done) cudaEventDestroy(t.ev_done);
+        if (t.stream) cudaStreamDestroy(t.stream);
+    };
+    if (cudaMalloc(&t.dev, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LCS_ENOMEM, "cudaMalloc of a batch");
+    }
+    t.bytes = total;
+    if (cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&t.ev_start) != cudaSuccess || cudaEventCreate(&t.ev_done) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, LCS_ECUDA, "batch stream/events");
+    }
+    t.d_lens = reinterpret_cast<int64_t *>(t.dev + o_lens);
+    t.d_strings = reinterpret_cast<uint8_t *>(t.dev + o_str);
+    t.d_err = reinterpret_cast<int *>(t.dev + o_err);
+    cudaStream_t st = t.stream;
+    std::vector<BatchPair> hp;
+    std::vector<int32_t> order;
+    for (int64_t q = 0; q < count; ++q) {
+        const lcs_pair &pr = pairs[q];
+        if (pr.m > max_rows) continue;
+        BatchPair b{};
+        b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
+        b.str_off = str_off[q] < 0 ? 0 : str_off[q];
+        b.scratch_off = scr_off[q];
+        b.len_out = t.d_lens + q;
+        b.want = str_off[q] >= 0 ? 1 : 0;
+        order.push_back((int32_t)hp.size());
+        hp.push_back(b);
+    }
+    // Largest pairs first, so that the last warps to finish have small ones.
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return hp[x].m * hp[x].n > hp[y].m * hp[y].n; });
+    lcs_status s = LCS_OK;
+    do {
+        if (cudaEventRecord(t.ev_start, st) != cudaSuccess ||
+            cudaMemsetAsync(t.dev + o_err, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(t.d_lens, 0, sizeof(int64_t) * std::max<int64_t>(1, count), st) != cudaSuccess) {
+            s = fail(ctx, LCS_ECUDA, "batch setup");
+            break;
+        }
+        // Pairs too tall for one strip: the strip tree, one after another.
+        for (int64_t q = 0; q < count && s == LCS_OK; ++q) {
+            const lcs_pair &pr = pairs[q];
+            if (pr.m <= max_rows) continue;
+            lcs_status ps = solve_device(ctx, pr.a, pr.m, pr.b, pr.n, LCS_I32, nullptr, 0,
+                                         str_off[q] >= 0 ? t.d_strings + str_off[q] : nullptr,
+                                         std::min(pr.m, pr.n), nullptr, t.d_lens + q, true, st);
+            if (ps == LCS_OK) ps = read_back(ctx, st, nullptr);
+            t.host_status[q] = ps;
+            if (ps == LCS_ECUDA) s = ps;
+        }
+        if (s != LCS_OK) break;
+        if (!hp.empty()) {
+            if (cudaMemcpyAsync(t.dev + o_pairs, hp.data(), sizeof(BatchPair) * hp.size(), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(t.dev + o_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess) {
+                s = fail(ctx, LCS_ECUDA, "batch descriptors");
+                break;
+            }
+            BatchParams bp{};
+            bp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_pairs);
+            bp.order = reinterpret_cast<const int32_t *>(t.dev + o_order);
+            bp.count = (int64_t)hp.size();
+            bp.scratch = reinterpret_cast<uint32_t *>(t.dev + o_scr);
+            bp.strings = t.d_strings;
+            bp.err = t.d_err;
+            if (launch_batch_small(bp, st) != cudaSuccess) {
+                s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+        }
+        // (The descriptor copies come from pageable host memory, which the
+        // runtime stages before cudaMemcpyAsync returns.)
+        if (cudaEventRecord(t.ev_done, st) != cudaSuccess) s = fail(ctx, LCS_ECUDA, "batch event");
+    } while (false);
+    if (s != LCS_OK) {
+        cudaStreamSynchronize(st);
+        cleanup();
+        return s;
+    }
+    const uint64_t id = ctx->next_ticket++;
+    ctx->batch_bytes += t.bytes;
+    ctx->peak = std::max(ctx->peak, ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes);
+    ctx->tickets.emplace(id, std::move(t));
+    *ticket_out = id;
+    return LCS_OK;
+}
+
+lcs_status lcs_batch_poll(lcs_ctx *ctx, uint64_t ticket, lcs_result *results, int64_t cap, int64_t *n_done,
+                          int32_t timeout_ms) {
+    if (!ctx || !n_done || cap < 0 || (cap > 0 && !results)) return LCS_EINVAL;
+    *n_done = 0;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, LCS_EINVAL, "unknown batch ticket");
+    BatchTicket &t = it->second;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    const double t0 = steady_seconds();
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(t.ev_done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(ctx, LCS_ECUDA, cudaGetErrorString(q));
+        if (timeout_ms >= 0 && (steady_seconds() - t0) * 1e3 >= timeout_ms) return LCS_OK;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    std::vector<int64_t> lens(t.count);
+    int err = 0;
+    if (t.count) LCS_CK(ctx, cudaMemcpy(lens.data(), t.d_lens, sizeof(int64_t) * t.count, cudaMemcpyDeviceToHost));
+    LCS_CK(ctx, cudaMemcpy(&err, t.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    float ms = 0.0f;
+    LCS_CK(ctx, cudaEventElapsedTime(&ms, t.ev_start, t.ev_done));
+    const lcs_status dev_status = (err & ERR_TIMEOUT) ? LCS_ETIMEOUT : (err ? LCS_ECUDA : LCS_OK);
+    const int64_t nw = std::min(cap, t.count);
+    for (int64_t q = 0; q < nw; ++q) {
+        lcs_result &r = results[q];
+        r.len = lens[q];
+        r.string_offset = t.str_off[q];
+        r.status = t.host_status[q] != LCS_OK ? t.host_status[q] : dev_status;
+        r.t_submit = t.t_submit;
+        r.t_done = t.t_submit + ms * 1e-3;
+    }
+    *n_done = t.count;
+    return cap < t.count ? fail(ctx, LCS_EOVERFLOW, "results capacity below the batch size") : LCS_OK;
+}
+
+lcs_status lcs_batch_strings(lcs_ctx *ctx, uint64_t ticket, uint8_t *out, int64_t cap, int64_t *bytes) {
+    if (!ctx || !bytes || cap < 0) return LCS_EINVAL;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, LCS_EINVAL, "unknown batch ticket");
+    BatchTicket &t = it->second;
+    *bytes = t.strings_bytes;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    LCS_CK(ctx, cudaEventSynchronize(t.ev_done));
+    if (cap < t.strings_bytes) return fail(ctx, LCS_EOVERFLOW, "string buffer too small");
+    if (t.strings_bytes > 0) {
+        if (!out) return LCS_EINVAL;
+        LCS_CK(ctx, cudaMemcpy(out, t.d_strings, (size_t)t.strings_bytes, cudaMemcpyDefault));
+    }
+    return LCS_OK;
+}
+
+lcs_status lcs_batch_release(lcs_ctx *ctx, uint64_t ticket) {
+    if (!ctx) return LCS_EINVAL;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, LCS_EINVAL, "unknown batch ticket");
+    BatchTicket &t = it->second;
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    LCS_CK(ctx, cudaStreamSynchronize(t.stream));
+    cudaFree(t.dev);
+    cudaEventDestroy(t.ev_start);
+    cudaEventDestroy(t.ev_done);
+    cudaStreamDestroy(t.stream);
+    ctx->batch_bytes -= t.bytes;
+    ctx->tickets.erase(it);
     return LCS_OK;
 }
 

@@ -70,6 +70,28 @@ cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStr
 // CTAs after the coarse levels.
 cudaError_t launch_tile_dpx(MergeParams p, int out_dtype, cudaStream_t st);
 
+// One pair of a batch on the one-strip path (batch.cu).
+struct BatchPair {
+    const uint8_t *a, *b;
+    int64_t m, n;
+    int64_t str_off;       // byte offset of the pair's LCS in BatchParams::strings
+    int64_t scratch_off;   // word offset of its (n+1) x ceil(m/32) column vectors
+    int64_t *len_out;      // device word receiving the length
+    int32_t want;          // store the columns and walk back for the LCS
+    int32_t pad;
+};
+struct BatchParams {
+    const BatchPair *pairs;
+    const int32_t *order;  // processing order (largest first), nullable
+    int64_t count;
+    uint32_t *scratch;
+    uint8_t *strings;
+    int *err;
+};
+// Every pair with 1 <= m <= batch_max_rows() on one launch, a warp per pair.
+cudaError_t launch_batch_small(const BatchParams &bp, cudaStream_t st);
+int batch_max_rows();
+
 // Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full
 // scans) then sigma0/2 .. 1 (windows bounded by the coarser level).
 cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st);
