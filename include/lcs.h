@@ -241,11 +241,12 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,
 /* ------------------------------------------------------------------------
  * Batches of independent pairs.  The paper treats one pair; serving many
  * pairs of uneven lengths is this library's extension of it.  A pair whose a
- * has at most 2048 letters is one strip (all its rows fit one bit vector), so
- * its tree has no merge level: the length is the strip's DIST(0, n) and one
- * LCS the strip's leftmost heaviest path, computed for every such pair of a
- * batch in one launch, a warp per pair.  Larger pairs go through the strip
- * tree of lcs_solve, one after another, inside lcs_batch_submit.
+ * has at most 16384 letters is one strip (all its rows fit one bit vector),
+ * so its tree has no merge level: the length is the strip's DIST(0, n) and
+ * one LCS the strip's leftmost heaviest path, computed a warp per pair in one
+ * launch per size class (a up to 2048, 4096, 8192, 16384 rows), the classes
+ * side by side.  Taller pairs go through the strip tree of lcs_solve, one
+ * after another, inside lcs_batch_submit.
  * ---------------------------------------------------------------------- */
 #define LCS_WANT_STRING 1u
 

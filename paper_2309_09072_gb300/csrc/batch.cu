@@ -1,113 +1,134 @@
-// batch.cu -- many independent pairs in one launch (lcs_batch_submit).
+// batch.cu -- many independent pairs in one submission (lcs_batch_submit).
 //
-// A pair whose string a has at most 2048 letters is one strip: its rows all
-// fit one bit vector of W = ceil(m / 32) <= 64 words, so the merge tree has
-// no level, the length is the strip's DIST(0, n) (Sec. I) and one LCS is the
+// A pair whose string a has at most 16384 letters is one strip: its rows all
+// fit one bit vector of W = ceil(m / 32) words, so the merge tree has no
+// level, the length is the strip's DIST(0, n) (Sec. I) and one LCS is the
 // strip's leftmost heaviest path from top vertex 0 to bottom vertex n
 // (Sec. II-C..II-E).  Only source 0 is needed, so a warp carries that one
 // source through the column sweep of the strip builder
-//     u = V & M[b_j];  V' = (V + u) | (V & ~M[b_j])
-// with the W words spread over the lanes (lane l holds words l and l + 32),
-// and the add's carries crossing the lanes by carry look-ahead: with G the
-// ballot of words whose sum overflowed and P the ballot of words that summed
-// to all ones (a carry in passes through them), the carries into the words
-// are the carries of the 32-bit addition (G | P) + G.
+//     u = V & M[b_j];  V' = (V + u) | (V & ~M[b_j]),
+// lane l holding the WPL consecutive words l*WPL .. l*WPL + WPL - 1.  The add
+// runs through a lane's words serially; its carries cross the lanes by carry
+// look-ahead: with G the ballot of lanes whose words overflowed and P the
+// ballot of lanes whose words summed to all ones (a carry in passes through
+// them), the carries into the lanes are the carries of the 32-bit addition
+// (G | P) + G.
 // Each column vector is stored when the pair wants its string; a backward
 // walk from (m, n) then keeps every row's segment as far left as it can go
 // (left while F keeps its value, else the match diagonal if it is tight,
 // else up), which is the leftmost heaviest path; a diagonal step into row r
 // marks a_r.  F(r, c) = r minus the ones among the first r bits of V_c is a
 // masked popcount reduced over the warp.
+#include <algorithm>
+
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
 namespace lcsg {
 
-constexpr int kBatchWarps = 4;           // warps (pairs in flight) per CTA
-constexpr int kBatchWords = 64;          // bit-vector words of the largest a (2048 rows)
 constexpr int kBatchLetters = 32;        // distinct letters of a with a shared mask table
 constexpr int kWalkCols = 16;            // column vectors staged per walk window
 
-struct BatchWarpSmem {
-    uint32_t msk[kBatchLetters][kBatchWords];   // row masks per letter of a
-    uint32_t win[kWalkCols][kBatchWords];       // the walk's window of column vectors
-    uint8_t a[kBatchWords * 32];                // the pair's a
-    uint8_t lmap[256];                          // letter -> mask row (255: not in a)
-    uint32_t present[8];                        // letters of a, one bit each
+// Per-warp shared memory of the words-per-lane class WPL.
+template <int WPL>
+struct BatchCfg {
+    static constexpr int W = 32 * WPL;                                  // words of the tallest a
+    static constexpr int kWarps = WPL <= 2 ? 4 : (WPL == 4 ? 2 : 1);    // warps (pairs in flight) per CTA
+    static constexpr size_t o_msk = 0;                                  // [kBatchLetters][W] row masks
+    static constexpr size_t o_win = o_msk + (size_t)kBatchLetters * W * 4;   // [kWalkCols][W] walk window
+    static constexpr size_t o_a = o_win + (size_t)kWalkCols * W * 4;    // the pair's a (32 W bytes)
+    static constexpr size_t o_lmap = o_a + (size_t)W * 32;              // letter -> mask row (255: absent)
+    static constexpr size_t o_present = o_lmap + 256;                   // letters of a, a bit each
+    static constexpr size_t warp_bytes = (o_present + 32 + 15) / 16 * 16;
 };
 
-// Carries into the 32 words of one half (bit l: into lane l's word), given
-// each lane's generate g and propagate p and the carry into the half; *cout
-// receives the carry out of its top word.
-__device__ __forceinline__ uint32_t carry_in(bool g, bool p, uint32_t cin, uint32_t *cout) {
+// Carries into the 32 lanes' word blocks (bit l: into lane l), given each
+// lane's generate g and propagate p.
+__device__ __forceinline__ uint32_t lane_carries(bool g, bool p) {
     const uint32_t G = __ballot_sync(0xFFFFFFFFu, g), P = __ballot_sync(0xFFFFFFFFu, p);
-    const uint64_t A = (uint64_t)(G | P), B = (uint64_t)G;
-    const uint64_t sum = A + B + cin;
-    *cout = (uint32_t)(sum >> 32);
-    return (uint32_t)(sum ^ A ^ B);
+    const uint32_t A = G | P;
+    return (A + G) ^ A ^ G;
 }
 
-__global__ void __launch_bounds__(kBatchWarps * 32) batch_small_kernel(BatchParams bp) {
+template <int WPL>
+__global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel(BatchParams bp) {
+    using C = BatchCfg<WPL>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BatchWarpSmem &S = reinterpret_cast<BatchWarpSmem *>(smem_raw)[warp];
-    const int64_t warps = (int64_t)gridDim.x * kBatchWarps;
-    for (int64_t q = (int64_t)blockIdx.x * kBatchWarps + warp; q < bp.count; q += warps) {
+    unsigned char *ws = smem_raw + warp * C::warp_bytes;
+    uint32_t(*msk)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(ws + C::o_msk);
+    uint32_t(*win)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(ws + C::o_win);
+    uint8_t *sa = ws + C::o_a;
+    uint8_t *lmap = ws + C::o_lmap;
+    uint32_t *present = reinterpret_cast<uint32_t *>(ws + C::o_present);
+    const int64_t warps = (int64_t)gridDim.x * C::kWarps;
+    for (int64_t q = (int64_t)blockIdx.x * C::kWarps + warp; q < bp.count; q += warps) {
         const BatchPair pr = bp.pairs[bp.order ? bp.order[q] : q];
         const int m = (int)pr.m;
         const int64_t n = pr.n;
-        if (m <= 0 || n <= 0) {
-            if (lane == 0) pr.len_out[0] = 0;
+        if (m <= 0 || n <= 0 || m > 32 * C::W) {
+            if (lane == 0) {
+                pr.len_out[0] = 0;
+                if (m > 32 * C::W) set_error(bp.err, ERR_BOUNDS);
+            }
             continue;
         }
-        const int W = (m + 31) >> 5;
+        const int Wu = (m + 31) >> 5;          // words in use; rows >= m are padding
         // Stage a, rank its letters, build the row masks.
-        for (int t = lane; t < 8; t += 32) S.present[t] = 0u;
+        if (lane < 8) present[lane] = 0u;
         __syncwarp();
         for (int r = lane; r < m; r += 32) {
             const uint8_t ch = pr.a[r];
-            S.a[r] = ch;
-            atomicOr(&S.present[ch >> 5], 1u << (ch & 31));
+            sa[r] = ch;
+            atomicOr(&present[ch >> 5], 1u << (ch & 31));
         }
         __syncwarp();
         int nlet = 0;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) nlet += __popc(S.present[t]);
+        for (int t = 0; t < 8; ++t) nlet += __popc(present[t]);
         const bool table = nlet <= kBatchLetters;
         if (table) {
             for (int c = lane; c < 256; c += 32) {
-                const uint32_t word = S.present[c >> 5], bit = 1u << (c & 31);
+                const uint32_t word = present[c >> 5], bit = 1u << (c & 31);
                 int rank = 0;
-                for (int t = 0; t < (c >> 5); ++t) rank += __popc(S.present[t]);
+                for (int t = 0; t < (c >> 5); ++t) rank += __popc(present[t]);
                 rank += __popc(word & (bit - 1u));
-                S.lmap[c] = (word & bit) ? (uint8_t)rank : (uint8_t)255;
+                lmap[c] = (word & bit) ? (uint8_t)rank : (uint8_t)255;
             }
-            for (int t = lane; t < nlet * kBatchWords; t += 32) (&S.msk[0][0])[t] = 0u;
+            for (int t = lane; t < nlet * C::W; t += 32) (&msk[0][0])[t] = 0u;
             __syncwarp();
-            for (int r = lane; r < m; r += 32) atomicOr(&S.msk[S.lmap[S.a[r]]][r >> 5], 1u << (r & 31));
+            for (int r = lane; r < m; r += 32) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
         }
         __syncwarp();
-        // Rows of lane l: word l (rows 32l..) and word l + 32; rows >= m are
-        // padding, set in V and never in a mask.
-        const bool hi_used = W > 32;
-        auto mask_of = [&](uint8_t ch, int w) -> uint32_t {
-            if (w >= W) return 0u;
+        const int w0 = lane * WPL;                // this lane's first word
+        auto masks = [&](uint8_t ch, uint32_t (&M)[WPL]) {
             if (table) {
-                const uint8_t k = S.lmap[ch];
-                return k == 255 ? 0u : S.msk[k][w];
+                const uint8_t k = lmap[ch];
+#pragma unroll
+                for (int t = 0; t < WPL; ++t) M[t] = (k == 255 || w0 + t >= Wu) ? 0u : msk[k][w0 + t];
+            } else {
+                // More than kBatchLetters letters in a: compare the rows.
+#pragma unroll
+                for (int t = 0; t < WPL; ++t) {
+                    uint32_t mk = 0u;
+                    const int r0 = (w0 + t) * 32;
+                    for (int b = 0; b < 32 && r0 + b < m; ++b) mk |= (uint32_t)(sa[r0 + b] == ch) << b;
+                    M[t] = mk;
+                }
             }
-            uint32_t mk = 0u;                    // more than kBatchLetters letters: compare
-            const int r0 = w * 32;
-            for (int t = 0; t < 32 && r0 + t < m; ++t) mk |= (uint32_t)(S.a[r0 + t] == ch) << t;
-            return mk;
         };
-        uint32_t V0 = 0xFFFFFFFFu, V1 = 0xFFFFFFFFu;
-        uint32_t *col = bp.scratch ? bp.scratch + pr.scratch_off : nullptr;   // (n+1) x W words
+        uint32_t V[WPL];
+#pragma unroll
+        for (int t = 0; t < WPL; ++t) V[t] = 0xFFFFFFFFu;
+        uint32_t *col = bp.scratch ? bp.scratch + pr.scratch_off : nullptr;   // (n+1) x Wu words
         const bool want = pr.want && col != nullptr;
-        if (want) {
-            if (lane < W) col[lane] = V0;
-            if (lane + 32 < W) col[lane + 32] = V1;
-        }
+        auto store_col = [&](int64_t c) {
+            uint32_t *cv = col + c * Wu;
+#pragma unroll
+            for (int t = 0; t < WPL; ++t)
+                if (w0 + t < Wu) cv[w0 + t] = V[t];
+        };
+        if (want) store_col(0);
         uint32_t bnext = (lane < n) ? pr.b[lane] : 0u;      // b[blk + lane], one block ahead
         for (int64_t blk = 0; blk < n; blk += 32) {
             const uint32_t bcur = bnext;
@@ -115,61 +136,66 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_small_kernel(BatchPara
             const int cnt = (int)min((int64_t)32, n - blk);
             for (int t = 0; t < cnt; ++t) {
                 const uint8_t ch = (uint8_t)__shfl_sync(0xFFFFFFFFu, bcur, t);
-                const uint32_t M0 = mask_of(ch, lane), M1 = hi_used ? mask_of(ch, lane + 32) : 0u;
-                const uint32_t u0 = V0 & M0, u1 = V1 & M1;
-                const uint32_t s0 = V0 + u0, s1 = V1 + u1;
-                uint32_t c_lo, dummy;
-                const uint32_t cin_lo = carry_in(s0 < V0, s0 == 0xFFFFFFFFu, 0u, &c_lo);
-                const uint32_t cin_hi = hi_used ? carry_in(s1 < V1, s1 == 0xFFFFFFFFu, c_lo, &dummy) : 0u;
-                const uint32_t f0 = s0 + ((cin_lo >> lane) & 1u), f1 = s1 + ((cin_hi >> lane) & 1u);
-                V0 = f0 | (V0 & ~M0);
-                V1 = f1 | (V1 & ~M1);
-                if (want) {
-                    uint32_t *cv = col + (blk + t + 1) * W;
-                    if (lane < W) cv[lane] = V0;
-                    if (lane + 32 < W) cv[lane + 32] = V1;
+                uint32_t M[WPL], s[WPL];
+                masks(ch, M);
+                // This lane's words of V + (V & M) with no carry in: generate
+                // and propagate of the lane.
+                uint32_t carry = 0u;
+                bool ones = true;
+#pragma unroll
+                for (int k = 0; k < WPL; ++k) {
+                    const uint64_t sum = (uint64_t)V[k] + (uint64_t)(V[k] & M[k]) + carry;
+                    s[k] = (uint32_t)sum;
+                    carry = (uint32_t)(sum >> 32);
+                    ones = ones && s[k] == 0xFFFFFFFFu;
                 }
+                uint32_t cin = (lane_carries(carry != 0u, ones) >> lane) & 1u;
+#pragma unroll
+                for (int k = 0; k < WPL; ++k) {
+                    const uint32_t sum = s[k] + cin;
+                    cin = (cin != 0u && sum == 0u) ? 1u : 0u;
+                    V[k] = sum | (V[k] & ~M[k]);
+                }
+                if (want) store_col(blk + t + 1);
             }
         }
         // Length = F(m, n) = zeros among the first m bits.
-        auto ones_below = [&](uint32_t v0, uint32_t v1, int r) -> int {
-            const int b0 = min(max(r - 32 * lane, 0), 32), b1 = min(max(r - 32 * (lane + 32), 0), 32);
-            const uint32_t m0 = b0 == 32 ? 0xFFFFFFFFu : ((1u << b0) - 1u);
-            const uint32_t m1 = b1 == 32 ? 0xFFFFFFFFu : ((1u << b1) - 1u);
-            return __reduce_add_sync(0xFFFFFFFFu, __popc(v0 & m0) + __popc(v1 & m1));
+        auto ones_below = [&](const uint32_t (&v)[WPL], int r) -> int {
+            int ones = 0;
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) {
+                const int bits = min(max(r - 32 * (w0 + k), 0), 32);
+                ones += __popc(v[k] & (bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u)));
+            }
+            return __reduce_add_sync(0xFFFFFFFFu, ones);
         };
-        const int L = m - ones_below(V0, V1, m);
+        const int L = m - ones_below(V, m);
         if (lane == 0) pr.len_out[0] = L;
         if (!want) continue;
         __syncwarp();
-        // Backward walk over the stored columns, a window of kWalkCols at a
-        // time in shared memory; the warp moves together (every lane computes
-        // the same F values).
-        // The walk asks for its current column c or c - 1, c never growing:
-        // a window that misses the asked column is reloaded to end one past
-        // it, so that it holds the current column as well.
-        int64_t wlo = 0, whi = -1;               // columns [wlo, whi] are staged
-        auto column = [&](int64_t c, uint32_t &v0, uint32_t &v1) {
+        // Backward walk over the stored columns, kWalkCols of them at a time
+        // in shared memory; the warp moves together (every lane computes the
+        // same F values).  The walk asks for its current column c or c - 1,
+        // c never growing: a window that misses the asked column is reloaded
+        // to end one past it, so that it holds the current column as well.
+        int64_t wlo = 0, whi = -1;
+        auto F = [&](int64_t c, int r) -> int {
             if (c < wlo || c > whi) {
                 __syncwarp();
                 whi = min(n, c + 1);
                 wlo = max((int64_t)0, whi - kWalkCols + 1);
                 const int64_t nc = whi - wlo + 1;
-                for (int64_t e = lane; e < nc * W; e += 32) {
-                    const int64_t cc = e / W;
-                    const int w = (int)(e - cc * W);
-                    S.win[cc][w] = col[(wlo + cc) * W + w];
+                for (int64_t e = lane; e < nc * Wu; e += 32) {
+                    const int64_t cc = e / Wu;
+                    const int w = (int)(e - cc * Wu);
+                    win[cc][w] = col[(wlo + cc) * Wu + w];
                 }
                 __syncwarp();
             }
-            const uint32_t *v = S.win[c - wlo];
-            v0 = lane < W ? v[lane] : 0xFFFFFFFFu;
-            v1 = lane + 32 < W ? v[lane + 32] : 0xFFFFFFFFu;
-        };
-        auto F = [&](int64_t c, int r) -> int {
-            uint32_t v0, v1;
-            column(c, v0, v1);
-            return r - ones_below(v0, v1, r);
+            uint32_t v[WPL];
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) v[k] = w0 + k < Wu ? win[c - wlo][w0 + k] : 0xFFFFFFFFu;
+            return r - ones_below(v, r);
         };
         uint8_t *str = bp.strings + pr.str_off;
         int r = m;
@@ -191,9 +217,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_small_kernel(BatchPara
                     --c;
                     continue;
                 }
-                if (S.a[r - 1] == bchar(c - 1) && F(c - 1, r - 1) == fc - 1) {   // diagonal into row r
+                if (sa[r - 1] == bchar(c - 1) && F(c - 1, r - 1) == fc - 1) {   // diagonal into row r
                     --pos;
-                    if (lane == 0 && pos >= 0) str[pos] = S.a[r - 1];
+                    if (lane == 0 && pos >= 0) str[pos] = sa[r - 1];
                     --r;
                     --c;
                     --fc;
@@ -207,24 +233,40 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_small_kernel(BatchPara
     }
 }
 
-size_t batch_smem_bytes() { return (size_t)kBatchWarps * sizeof(BatchWarpSmem); }
-int batch_max_rows() { return kBatchWords * 32; }
+int batch_max_rows() { return 32 * BatchCfg<16>::W; }
 
-cudaError_t launch_batch_small(const BatchParams &bp, cudaStream_t st) {
-    if (bp.count <= 0) return cudaSuccess;
-    const size_t smem = batch_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int batch_words_per_lane(int64_t m) {
+    const int64_t w = (m + 31) / 32;
+    return w <= 64 ? 2 : (w <= 128 ? 4 : (w <= 256 ? 8 : 16));
+}
+
+template <int WPL>
+static cudaError_t launch_wpl(const BatchParams &bp, cudaStream_t st) {
+    using C = BatchCfg<WPL>;
+    const size_t smem = (size_t)C::kWarps * C::warp_bytes;
+    auto kern = batch_strip_kernel<WPL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_small_kernel, kBatchWarps * 32, smem)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::kWarps * 32, smem)) != cudaSuccess)
         return e;
-    const int64_t need = ceil_div(bp.count, kBatchWarps);
+    const int64_t need = ceil_div(bp.count, C::kWarps);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * std::max(per_sm, 1)));
-    batch_small_kernel<<<(unsigned)grid, kBatchWarps * 32, smem, st>>>(bp);
+    kern<<<(unsigned)grid, C::kWarps * 32, smem, st>>>(bp);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_strip(const BatchParams &bp, int wpl, cudaStream_t st) {
+    if (bp.count <= 0) return cudaSuccess;
+    switch (wpl) {
+        case 2: return launch_wpl<2>(bp, st);
+        case 4: return launch_wpl<4>(bp, st);
+        case 8: return launch_wpl<8>(bp, st);
+        case 16: return launch_wpl<16>(bp, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace lcsg

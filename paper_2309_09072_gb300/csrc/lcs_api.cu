@@ -87,10 +87,13 @@ constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int6
 
 // A submitted batch: its stream, completion events and one device block
 // holding descriptors, lengths, strings, column vectors and an error word.
+constexpr int kBatchClasses = 4;       // words per lane 2, 4, 8, 16
 struct BatchTicket {
     int64_t count = 0;
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaStream_t aux[kBatchClasses] = {};  // one per words-per-lane class, forked from `stream`
+    cudaEvent_t ev_join[kBatchClasses] = {};
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_fork = nullptr;
     double t_submit = 0.0;
     char *dev = nullptr;
     size_t bytes = 0;
@@ -672,7 +675,12 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
         if (t.dev) cudaFree(t.dev);
         if (t.ev_start) cudaEventDestroy(t.ev_start);
         if (t.ev_done) cudaEventDestroy(t.ev_done);
+        if (t.ev_fork) cudaEventDestroy(t.ev_fork);
         if (t.stream) cudaStreamDestroy(t.stream);
+        for (int c = 0; c < kBatchClasses; ++c) {
+            if (t.aux[c]) cudaStreamDestroy(t.aux[c]);
+            if (t.ev_join[c]) cudaEventDestroy(t.ev_join[c]);
+        }
     }
     for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
@@ -953,15 +961,25 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         if (t.dev) cudaFree(t.dev);
         if (t.ev_start) cudaEventDestroy(t.ev_start);
         if (t.ev_done) cudaEventDestroy(t.ev_done);
+        if (t.ev_fork) cudaEventDestroy(t.ev_fork);
         if (t.stream) cudaStreamDestroy(t.stream);
+        for (int c = 0; c < kBatchClasses; ++c) {
+            if (t.aux[c]) cudaStreamDestroy(t.aux[c]);
+            if (t.ev_join[c]) cudaEventDestroy(t.ev_join[c]);
+        }
     };
     if (cudaMalloc(&t.dev, total) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, LCS_ENOMEM, "cudaMalloc of a batch");
     }
     t.bytes = total;
-    if (cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&t.ev_start) != cudaSuccess || cudaEventCreate(&t.ev_done) != cudaSuccess) {
+    bool ok = cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&t.ev_start) == cudaSuccess && cudaEventCreate(&t.ev_done) == cudaSuccess &&
+              cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; ok && c < kBatchClasses; ++c)
+        ok = cudaStreamCreateWithFlags(&t.aux[c], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&t.ev_join[c], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cleanup();
         return fail(ctx, LCS_ECUDA, "batch stream/events");
     }
@@ -969,23 +987,33 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     t.d_strings = reinterpret_cast<uint8_t *>(t.dev + o_str);
     t.d_err = reinterpret_cast<int *>(t.dev + o_err);
     cudaStream_t st = t.stream;
+    // Descriptors by words-per-lane class (class c holds a up to 2048 << c
+    // rows), each class's processing order largest pair first, so that the
+    // last warps to finish have small ones.
     std::vector<BatchPair> hp;
     std::vector<int32_t> order;
-    for (int64_t q = 0; q < count; ++q) {
-        const lcs_pair &pr = pairs[q];
-        if (pr.m > max_rows) continue;
-        BatchPair b{};
-        b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
-        b.str_off = str_off[q] < 0 ? 0 : str_off[q];
-        b.scratch_off = scr_off[q];
-        b.len_out = t.d_lens + q;
-        b.want = str_off[q] >= 0 ? 1 : 0;
-        order.push_back((int32_t)hp.size());
-        hp.push_back(b);
+    int64_t cls_begin[kBatchClasses + 1] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < kBatchClasses; ++c) {
+        const int wpl = 2 << c;
+        cls_begin[c] = (int64_t)hp.size();
+        for (int64_t q = 0; q < count; ++q) {
+            const lcs_pair &pr = pairs[q];
+            if (pr.m > max_rows || batch_words_per_lane(pr.m) != wpl) continue;
+            BatchPair b{};
+            b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
+            b.str_off = str_off[q] < 0 ? 0 : str_off[q];
+            b.scratch_off = scr_off[q];
+            b.len_out = t.d_lens + q;
+            b.want = str_off[q] >= 0 ? 1 : 0;
+            order.push_back((int32_t)(hp.size() - cls_begin[c]));
+            hp.push_back(b);
+        }
+        std::stable_sort(order.begin() + cls_begin[c], order.end(), [&](int32_t x, int32_t y) {
+            const BatchPair &u = hp[cls_begin[c] + x], &v = hp[cls_begin[c] + y];
+            return u.m * u.n > v.m * v.n;
+        });
     }
-    // Largest pairs first, so that the last warps to finish have small ones.
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t x, int32_t y) { return hp[x].m * hp[x].n > hp[y].m * hp[y].n; });
+    cls_begin[kBatchClasses] = (int64_t)hp.size();
     lcs_status s = LCS_OK;
     do {
         if (cudaEventRecord(t.ev_start, st) != cudaSuccess ||
@@ -1014,17 +1042,29 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
                 s = fail(ctx, LCS_ECUDA, "batch descriptors");
                 break;
             }
-            BatchParams bp{};
-            bp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_pairs);
-            bp.order = reinterpret_cast<const int32_t *>(t.dev + o_order);
-            bp.count = (int64_t)hp.size();
-            bp.scratch = reinterpret_cast<uint32_t *>(t.dev + o_scr);
-            bp.strings = t.d_strings;
-            bp.err = t.d_err;
-            if (launch_batch_small(bp, st) != cudaSuccess) {
-                s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
+            // The classes run side by side, each on a stream forked from
+            // the batch's and joined back before ev_done.
+            if (cudaEventRecord(t.ev_fork, st) != cudaSuccess) {
+                s = fail(ctx, LCS_ECUDA, "batch fork");
                 break;
             }
+            for (int c = 0; c < kBatchClasses && s == LCS_OK; ++c) {
+                const int64_t k0 = cls_begin[c], k1 = cls_begin[c + 1];
+                if (k1 == k0) continue;
+                BatchParams bp{};
+                bp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_pairs) + k0;
+                bp.order = reinterpret_cast<const int32_t *>(t.dev + o_order) + k0;
+                bp.count = k1 - k0;
+                bp.scratch = reinterpret_cast<uint32_t *>(t.dev + o_scr);
+                bp.strings = t.d_strings;
+                bp.err = t.d_err;
+                if (cudaStreamWaitEvent(t.aux[c], t.ev_fork, 0) != cudaSuccess ||
+                    launch_batch_strip(bp, 2 << c, t.aux[c]) != cudaSuccess ||
+                    cudaEventRecord(t.ev_join[c], t.aux[c]) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, t.ev_join[c], 0) != cudaSuccess)
+                    s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
+            }
+            if (s != LCS_OK) break;
         }
         // (The descriptor copies come from pageable host memory, which the
         // runtime stages before cudaMemcpyAsync returns.)
@@ -1035,6 +1075,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         cleanup();
         return s;
     }
+    (void)ok;
     const uint64_t id = ctx->next_ticket++;
     ctx->batch_bytes += t.bytes;
     ctx->peak = std::max(ctx->peak, ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes);
@@ -1105,7 +1146,12 @@ lcs_status lcs_batch_release(lcs_ctx *ctx, uint64_t ticket) {
     cudaFree(t.dev);
     cudaEventDestroy(t.ev_start);
     cudaEventDestroy(t.ev_done);
+    cudaEventDestroy(t.ev_fork);
     cudaStreamDestroy(t.stream);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        cudaStreamDestroy(t.aux[c]);
+        cudaEventDestroy(t.ev_join[c]);
+    }
     ctx->batch_bytes -= t.bytes;
     ctx->tickets.erase(it);
     return LCS_OK;

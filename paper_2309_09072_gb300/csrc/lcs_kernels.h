@@ -88,8 +88,10 @@ struct BatchParams {
     uint8_t *strings;
     int *err;
 };
-// Every pair with 1 <= m <= batch_max_rows() on one launch, a warp per pair.
-cudaError_t launch_batch_small(const BatchParams &bp, cudaStream_t st);
+// The pairs of one words-per-lane class wpl (2, 4, 8 or 16: a up to
+// 1024 wpl rows) on one launch, a warp per pair.
+cudaError_t launch_batch_strip(const BatchParams &bp, int wpl, cudaStream_t st);
+int batch_words_per_lane(int64_t m);
 int batch_max_rows();
 
 // Coarse argmax on the T-grid: one launch per level, sigma = sigma0 (full

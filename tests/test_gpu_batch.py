@@ -75,7 +75,12 @@ def test_batch_edge_cases(ctx):
         (acgt[:1], acgt[:1]),                                    # 1 x 1 match
         (acgt[:1], acgt[1:2]),                                   # 1 x 1 mismatch
         (inputs.uniform(rng, 2048, acgt), inputs.uniform(rng, 700, acgt)),      # 64 words, tallest strip
-        (inputs.uniform(rng, 2049, acgt), inputs.uniform(rng, 300, acgt)),      # too tall: the strip tree
+        (inputs.uniform(rng, 2049, acgt), inputs.uniform(rng, 300, acgt)),      # next size class
+        (inputs.uniform(rng, 4096, acgt), inputs.uniform(rng, 500, acgt)),
+        (inputs.uniform(rng, 4097, acgt), inputs.uniform(rng, 500, acgt)),
+        (inputs.uniform(rng, 8193, acgt), inputs.uniform(rng, 200, acgt)),
+        (inputs.uniform(rng, 16384, acgt), inputs.uniform(rng, 150, acgt)),    # tallest one-strip pair
+        (inputs.uniform(rng, 16385, acgt), inputs.uniform(rng, 120, acgt)),    # too tall: the strip tree
         (inputs.uniform(rng, 33, acgt), inputs.uniform(rng, 5000, acgt)),       # two words, long b
         (inputs.uniform(rng, 300, many), inputs.uniform(rng, 400, many)),       # > 32 letters in a
         (inputs.uniform(rng, 1100, acgt),) * 2,                                  # identical
@@ -86,6 +91,30 @@ def test_batch_edge_cases(ctx):
     pairs = [p if len(p) != 2 or p[0] is not p[1] else (p[0], p[1].copy()) for p in pairs]
     res, strings = run_batch(ctx, pairs)
     check_exact(pairs, res, strings)
+
+
+def test_batch_serving_mix(ctx):
+    # Requests shaped like the serving workload (20-letter alphabet, 30% of
+    # pairs correlated, lengths log-uniform, one m = n pair per batch taller
+    # than 2048): exact against the oracle, and the same results whether a
+    # pair runs alone or in the mix.
+    rng = np.random.default_rng(21)
+    alph = np.arange(20, dtype=np.uint8) + 65
+    ms = inputs.loguniform_lengths(rng, 40, 128, 3000)
+    pairs = []
+    for k, m in enumerate(ms):
+        a = inputs.uniform(rng, int(m), alph)
+        if k % 10 < 3:
+            b = inputs.mutate(rng, a, 0.10, 0.05, alph)
+        else:
+            b = inputs.uniform(rng, int(inputs.loguniform_lengths(rng, 1, 128, 3000)[0]), alph)
+        pairs.append((a, b))
+    res, strings = run_batch(ctx, pairs)
+    check_exact(pairs, res, strings)
+    for k in (0, 7, 33):
+        r1, s1 = run_batch(ctx, [pairs[k]])
+        assert r1[0]["len"] == res[k]["len"]
+        assert s1[: r1[0]["len"]] == strings[res[k]["string_offset"]: res[k]["string_offset"] + res[k]["len"]]
 
 
 def test_batch_matches_single_pair_path(ctx):
