@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -275,6 +276,26 @@ def batched_measure(B, torch, plain_pairs, reps=3):
             "batched_over_plain": bv / pv}
 
 
+def serving_measure(B, torch, seconds):
+    """The serving workload (Poisson arrivals at 2,000 pairs/s, 20 letters,
+    lengths log-uniform in [128, 8192], every 50th pair 16384 x 16384, 30%
+    correlated) for `seconds` seconds of arrivals through continuous batching
+    (serve.py over lcs_batch_submit/poll), strings resident on the device."""
+    from paper_2309_09072_gb300 import inputs, serve
+    times, pairs = inputs.serving_requests(duration_s=seconds)
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
+    ctx = B.lcs_create(0, 0)
+    serve.serve(ctx, dev[:50], times[:50] - times[0])          # warm-up on the first requests
+    out = serve.serve(ctx, dev, times)
+    B.lcs_destroy(ctx)
+    summ = serve.summary(out, [(len(a), len(b)) for a, b in pairs])
+    summ.update({"workload": "serving: Poisson 2,000 pairs/s for %.0f s, 20 letters, lengths log-uniform "
+                             "[128, 8192], every 50th pair 16384 x 16384, 30%% correlated; one LCS per pair"
+                             % seconds,
+                 "latency": "device completion of the request's batch minus its arrival"})
+    return summ
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -377,6 +398,8 @@ def run_ours(args):
     B.lcs_destroy(ctx)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_measure(B, torch, args.plain_pairs)
+    if rank == 0 and args.serve_seconds > 0:
+        line["serving"] = serving_measure(B, torch, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, b)
     if rank == 0:

@@ -13,12 +13,14 @@
 // ballot of lanes whose words summed to all ones (a carry in passes through
 // them), the carries into the lanes are the carries of the 32-bit addition
 // (G | P) + G.
-// Each column vector is stored when the pair wants its string; a backward
-// walk from (m, n) then keeps every row's segment as far left as it can go
-// (left while F keeps its value, else the match diagonal if it is tight,
-// else up), which is the leftmost heaviest path; a diagonal step into row r
-// marks a_r.  F(r, c) = r minus the ones among the first r bits of V_c is a
-// masked popcount reduced over the warp.
+// Each column vector, with the count of ones below each of its words, is
+// stored when the pair wants its string; a backward walk from (m, n) then
+// keeps every row's segment as far left as it can go (left while F keeps its
+// value, else the match diagonal if it is tight, else up), which is the
+// leftmost heaviest path; a diagonal step into row r marks a_r.  F(r, c) = r
+// minus the ones among the first r bits of V_c is one stored count plus one
+// masked popcount, read from a small shared-memory window of the columns and
+// words the walk is at.
 #include <algorithm>
 
 #include "lcs_common.cuh"
@@ -27,7 +29,7 @@
 namespace lcsg {
 
 constexpr int kBatchLetters = 32;        // distinct letters of a with a shared mask table
-constexpr int kWalkCols = 16;            // column vectors staged per walk window
+constexpr int kWalkCols = 32;            // columns staged per walk window (a lane each)
 
 // Per-warp shared memory of the words-per-lane class WPL.
 template <int WPL>
@@ -35,8 +37,9 @@ struct BatchCfg {
     static constexpr int W = 32 * WPL;                                  // words of the tallest a
     static constexpr int kWarps = WPL <= 2 ? 4 : (WPL == 4 ? 2 : 1);    // warps (pairs in flight) per CTA
     static constexpr size_t o_msk = 0;                                  // [kBatchLetters][W] row masks
-    static constexpr size_t o_win = o_msk + (size_t)kBatchLetters * W * 4;   // [kWalkCols][W] walk window
-    static constexpr size_t o_a = o_win + (size_t)kWalkCols * W * 4;    // the pair's a (32 W bytes)
+    static constexpr size_t o_win = o_msk + (size_t)kBatchLetters * W * 4;   // walk window: [kWalkCols][2]
+                                                                        // words, then [kWalkCols][2] counts
+    static constexpr size_t o_a = o_win + (size_t)kWalkCols * 2 * 4 + (size_t)kWalkCols * 2 * 4;
     static constexpr size_t o_lmap = o_a + (size_t)W * 32;              // letter -> mask row (255: absent)
     static constexpr size_t o_present = o_lmap + 256;                   // letters of a, a bit each
     static constexpr size_t warp_bytes = (o_present + 32 + 15) / 16 * 16;
@@ -57,7 +60,8 @@ __global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *ws = smem_raw + warp * C::warp_bytes;
     uint32_t(*msk)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(ws + C::o_msk);
-    uint32_t(*win)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(ws + C::o_win);
+    uint32_t(*wword)[2] = reinterpret_cast<uint32_t(*)[2]>(ws + C::o_win);
+    uint32_t(*wcnt)[2] = reinterpret_cast<uint32_t(*)[2]>(ws + C::o_win + kWalkCols * 2 * 4);
     uint8_t *sa = ws + C::o_a;
     uint8_t *lmap = ws + C::o_lmap;
     uint32_t *present = reinterpret_cast<uint32_t *>(ws + C::o_present);
@@ -120,13 +124,35 @@ __global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel
         uint32_t V[WPL];
 #pragma unroll
         for (int t = 0; t < WPL; ++t) V[t] = 0xFFFFFFFFu;
-        uint32_t *col = bp.scratch ? bp.scratch + pr.scratch_off : nullptr;   // (n+1) x Wu words
+        // Scratch of a pair that wants its string: (n+1) x Wu column words,
+        // then (n+1) x (Wu+1) 16-bit counts of the ones below each word
+        // (entry Wu: all of them).
+        uint32_t *col = bp.scratch ? bp.scratch + pr.scratch_off : nullptr;
+        uint16_t *cnt = col ? reinterpret_cast<uint16_t *>(col + (n + 1) * Wu) : nullptr;
         const bool want = pr.want && col != nullptr;
         auto store_col = [&](int64_t c) {
             uint32_t *cv = col + c * Wu;
+            uint16_t *pv = cnt + c * (Wu + 1);
+            int ones[WPL], tot = 0;
 #pragma unroll
-            for (int t = 0; t < WPL; ++t)
+            for (int t = 0; t < WPL; ++t) {
+                ones[t] = w0 + t < Wu ? __popc(V[t]) : 0;
+                tot += ones[t];
+            }
+            int below = tot;                      // inclusive scan of the lanes' totals
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, below, off);
+                if (lane >= off) below += y;
+            }
+            below -= tot;
+#pragma unroll
+            for (int t = 0; t < WPL; ++t) {
+                if (w0 + t <= Wu) pv[w0 + t] = (uint16_t)below;
                 if (w0 + t < Wu) cv[w0 + t] = V[t];
+                below += ones[t];
+            }
+            if (lane == 31 && Wu == C::W) pv[Wu] = (uint16_t)below;   // no lane holds index Wu
         };
         if (want) store_col(0);
         uint32_t bnext = (lane < n) ? pr.b[lane] : 0u;      // b[blk + lane], one block ahead
@@ -173,29 +199,36 @@ __global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel
         if (lane == 0) pr.len_out[0] = L;
         if (!want) continue;
         __syncwarp();
-        // Backward walk over the stored columns, kWalkCols of them at a time
-        // in shared memory; the warp moves together (every lane computes the
-        // same F values).  The walk asks for its current column c or c - 1,
-        // c never growing: a window that misses the asked column is reloaded
-        // to end one past it, so that it holds the current column as well.
+        // Backward walk.  F(r, c) needs word w = r / 32 of V_c and the count
+        // of ones below it; the window holds words w-1 and w (and their
+        // counts) of kWalkCols columns, a lane loading one column.  The walk
+        // asks for its current column c or c - 1 with c never growing, and
+        // for rows that never grow: a window that misses is reloaded to end
+        // one column past the asked one and to hold the asked word on top.
         int64_t wlo = 0, whi = -1;
+        int wbase = -2;                          // words wbase, wbase + 1 are staged
         auto F = [&](int64_t c, int r) -> int {
-            if (c < wlo || c > whi) {
+            const int w = r >> 5, bits = r & 31;
+            if (c < wlo || c > whi || w < wbase || w > wbase + 1) {
                 __syncwarp();
                 whi = min(n, c + 1);
                 wlo = max((int64_t)0, whi - kWalkCols + 1);
-                const int64_t nc = whi - wlo + 1;
-                for (int64_t e = lane; e < nc * Wu; e += 32) {
-                    const int64_t cc = e / Wu;
-                    const int w = (int)(e - cc * Wu);
-                    win[cc][w] = col[(wlo + cc) * Wu + w];
+                wbase = max(0, w - 1);
+                const int64_t cc = wlo + lane;
+                if (cc <= whi) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int wk = wbase + k;
+                        wword[lane][k] = wk < Wu ? col[cc * Wu + wk] : 0u;
+                        wcnt[lane][k] = wk <= Wu ? cnt[cc * (Wu + 1) + wk] : 0u;
+                    }
                 }
                 __syncwarp();
             }
-            uint32_t v[WPL];
-#pragma unroll
-            for (int k = 0; k < WPL; ++k) v[k] = w0 + k < Wu ? win[c - wlo][w0 + k] : 0xFFFFFFFFu;
-            return r - ones_below(v, r);
+            const int slot = (int)(c - wlo), k = w - wbase;
+            int ones = (int)wcnt[slot][k];
+            if (bits) ones += __popc(wword[slot][k] & ((1u << bits) - 1u));
+            return r - ones;
         };
         uint8_t *str = bp.strings + pr.str_off;
         int r = m;

@@ -88,12 +88,41 @@ constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int6
 // A submitted batch: its stream, completion events and one device block
 // holding descriptors, lengths, strings, column vectors and an error word.
 constexpr int kBatchClasses = 4;       // words per lane 2, 4, 8, 16
-struct BatchTicket {
-    int64_t count = 0;
+// The streams and events of one batch in flight, reused across batches.
+struct BatchLane {
     cudaStream_t stream = nullptr;
     cudaStream_t aux[kBatchClasses] = {};  // one per words-per-lane class, forked from `stream`
     cudaEvent_t ev_join[kBatchClasses] = {};
     cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_fork = nullptr;
+};
+void destroy_lane(BatchLane &l) {
+    if (l.stream) cudaStreamDestroy(l.stream);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (l.aux[c]) cudaStreamDestroy(l.aux[c]);
+        if (l.ev_join[c]) cudaEventDestroy(l.ev_join[c]);
+    }
+    if (l.ev_start) cudaEventDestroy(l.ev_start);
+    if (l.ev_done) cudaEventDestroy(l.ev_done);
+    if (l.ev_fork) cudaEventDestroy(l.ev_fork);
+    l = BatchLane{};
+}
+bool create_lane(BatchLane &l) {
+    bool ok = cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&l.ev_start) == cudaSuccess && cudaEventCreate(&l.ev_done) == cudaSuccess &&
+              cudaEventCreateWithFlags(&l.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; ok && c < kBatchClasses; ++c)
+        ok = cudaStreamCreateWithFlags(&l.aux[c], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&l.ev_join[c], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        destroy_lane(l);
+    }
+    return ok;
+}
+
+struct BatchTicket {
+    int64_t count = 0;
+    BatchLane lane;
     double t_submit = 0.0;
     char *dev = nullptr;
     size_t bytes = 0;
@@ -135,6 +164,8 @@ struct lcs_ctx {
     std::map<uint64_t, BatchTicket> tickets;
     uint64_t next_ticket = 1;
     size_t batch_bytes = 0;
+    std::vector<BatchLane> free_lanes;    // streams/events of released batches
+    cudaMemPool_t mempool = nullptr;      // batches' device memory (stream ordered, no device sync)
 };
 
 namespace {
@@ -672,16 +703,12 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     if (ctx->io) cudaFree(ctx->io);
     for (auto &kv : ctx->tickets) {
         BatchTicket &t = kv.second;
-        if (t.dev) cudaFree(t.dev);
-        if (t.ev_start) cudaEventDestroy(t.ev_start);
-        if (t.ev_done) cudaEventDestroy(t.ev_done);
-        if (t.ev_fork) cudaEventDestroy(t.ev_fork);
-        if (t.stream) cudaStreamDestroy(t.stream);
-        for (int c = 0; c < kBatchClasses; ++c) {
-            if (t.aux[c]) cudaStreamDestroy(t.aux[c]);
-            if (t.ev_join[c]) cudaEventDestroy(t.ev_join[c]);
-        }
+        if (t.dev) cudaFreeAsync(t.dev, t.lane.stream);
+        cudaStreamSynchronize(t.lane.stream);
+        destroy_lane(t.lane);
     }
+    for (auto &l : ctx->free_lanes) destroy_lane(l);
+    if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
     for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
@@ -936,8 +963,11 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         if (pr.m <= max_rows) {
             ++n_small;
             if (want && pr.m > 0 && pr.n > 0) {
+                // (n+1) column words per row word, then (n+1) x (words+1)
+                // 16-bit counts (batch.cu), rounded to 16 bytes.
+                const int64_t wu = (pr.m + 31) / 32;
                 scr_off[q] = scr_words;
-                scr_words += (pr.n + 1) * ((pr.m + 31) / 32);
+                scr_words += ((pr.n + 1) * wu + ((pr.n + 1) * (wu + 1) + 1) / 2 + 3) / 4 * 4;
             }
         }
     }
@@ -957,36 +987,44 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     t.strings_bytes = str_bytes;
     t.host_status.assign(count, LCS_OK);
     t.t_submit = steady_seconds();
-    auto cleanup = [&]() {
-        if (t.dev) cudaFree(t.dev);
-        if (t.ev_start) cudaEventDestroy(t.ev_start);
-        if (t.ev_done) cudaEventDestroy(t.ev_done);
-        if (t.ev_fork) cudaEventDestroy(t.ev_fork);
-        if (t.stream) cudaStreamDestroy(t.stream);
-        for (int c = 0; c < kBatchClasses; ++c) {
-            if (t.aux[c]) cudaStreamDestroy(t.aux[c]);
-            if (t.ev_join[c]) cudaEventDestroy(t.ev_join[c]);
+    // A lane (streams, events) from the free list, memory from the
+    // context's pool: no call here synchronises the device, so a batch
+    // submitted while others run overlaps with them.
+    if (!ctx->mempool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        if (cudaMemPoolCreate(&ctx->mempool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->mempool = nullptr;
+            return fail(ctx, LCS_ECUDA, "batch memory pool");
         }
+        uint64_t keep = UINT64_MAX;               // keep freed blocks for the next batches
+        cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (!ctx->free_lanes.empty()) {
+        t.lane = ctx->free_lanes.back();
+        ctx->free_lanes.pop_back();
+    } else if (!create_lane(t.lane)) {
+        return fail(ctx, LCS_ECUDA, "batch streams/events");
+    }
+    auto cleanup = [&]() {
+        if (t.dev) cudaFreeAsync(t.dev, t.lane.stream);
+        cudaStreamSynchronize(t.lane.stream);
+        ctx->free_lanes.push_back(t.lane);
     };
-    if (cudaMalloc(&t.dev, total) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&t.dev), total, ctx->mempool, t.lane.stream) != cudaSuccess) {
         cudaGetLastError();
-        return fail(ctx, LCS_ENOMEM, "cudaMalloc of a batch");
+        t.dev = nullptr;
+        cleanup();
+        return fail(ctx, LCS_ENOMEM, "batch device memory");
     }
     t.bytes = total;
-    bool ok = cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreate(&t.ev_start) == cudaSuccess && cudaEventCreate(&t.ev_done) == cudaSuccess &&
-              cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int c = 0; ok && c < kBatchClasses; ++c)
-        ok = cudaStreamCreateWithFlags(&t.aux[c], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&t.ev_join[c], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        cleanup();
-        return fail(ctx, LCS_ECUDA, "batch stream/events");
-    }
     t.d_lens = reinterpret_cast<int64_t *>(t.dev + o_lens);
     t.d_strings = reinterpret_cast<uint8_t *>(t.dev + o_str);
     t.d_err = reinterpret_cast<int *>(t.dev + o_err);
-    cudaStream_t st = t.stream;
+    cudaStream_t st = t.lane.stream;
     // Descriptors by words-per-lane class (class c holds a up to 2048 << c
     // rows), each class's processing order largest pair first, so that the
     // last warps to finish have small ones.
@@ -1016,7 +1054,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     cls_begin[kBatchClasses] = (int64_t)hp.size();
     lcs_status s = LCS_OK;
     do {
-        if (cudaEventRecord(t.ev_start, st) != cudaSuccess ||
+        if (cudaEventRecord(t.lane.ev_start, st) != cudaSuccess ||
             cudaMemsetAsync(t.dev + o_err, 0, sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(t.d_lens, 0, sizeof(int64_t) * std::max<int64_t>(1, count), st) != cudaSuccess) {
             s = fail(ctx, LCS_ECUDA, "batch setup");
@@ -1044,7 +1082,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             }
             // The classes run side by side, each on a stream forked from
             // the batch's and joined back before ev_done.
-            if (cudaEventRecord(t.ev_fork, st) != cudaSuccess) {
+            if (cudaEventRecord(t.lane.ev_fork, st) != cudaSuccess) {
                 s = fail(ctx, LCS_ECUDA, "batch fork");
                 break;
             }
@@ -1058,24 +1096,22 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
                 bp.scratch = reinterpret_cast<uint32_t *>(t.dev + o_scr);
                 bp.strings = t.d_strings;
                 bp.err = t.d_err;
-                if (cudaStreamWaitEvent(t.aux[c], t.ev_fork, 0) != cudaSuccess ||
-                    launch_batch_strip(bp, 2 << c, t.aux[c]) != cudaSuccess ||
-                    cudaEventRecord(t.ev_join[c], t.aux[c]) != cudaSuccess ||
-                    cudaStreamWaitEvent(st, t.ev_join[c], 0) != cudaSuccess)
+                if (cudaStreamWaitEvent(t.lane.aux[c], t.lane.ev_fork, 0) != cudaSuccess ||
+                    launch_batch_strip(bp, 2 << c, t.lane.aux[c]) != cudaSuccess ||
+                    cudaEventRecord(t.lane.ev_join[c], t.lane.aux[c]) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, t.lane.ev_join[c], 0) != cudaSuccess)
                     s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
             }
             if (s != LCS_OK) break;
         }
         // (The descriptor copies come from pageable host memory, which the
         // runtime stages before cudaMemcpyAsync returns.)
-        if (cudaEventRecord(t.ev_done, st) != cudaSuccess) s = fail(ctx, LCS_ECUDA, "batch event");
+        if (cudaEventRecord(t.lane.ev_done, st) != cudaSuccess) s = fail(ctx, LCS_ECUDA, "batch event");
     } while (false);
     if (s != LCS_OK) {
-        cudaStreamSynchronize(st);
         cleanup();
         return s;
     }
-    (void)ok;
     const uint64_t id = ctx->next_ticket++;
     ctx->batch_bytes += t.bytes;
     ctx->peak = std::max(ctx->peak, ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes);
@@ -1094,7 +1130,7 @@ lcs_status lcs_batch_poll(lcs_ctx *ctx, uint64_t ticket, lcs_result *results, in
     LCS_CK(ctx, cudaSetDevice(ctx->device));
     const double t0 = steady_seconds();
     for (;;) {
-        const cudaError_t q = cudaEventQuery(t.ev_done);
+        const cudaError_t q = cudaEventQuery(t.lane.ev_done);
         if (q == cudaSuccess) break;
         if (q != cudaErrorNotReady) return fail(ctx, LCS_ECUDA, cudaGetErrorString(q));
         if (timeout_ms >= 0 && (steady_seconds() - t0) * 1e3 >= timeout_ms) return LCS_OK;
@@ -1105,7 +1141,7 @@ lcs_status lcs_batch_poll(lcs_ctx *ctx, uint64_t ticket, lcs_result *results, in
     if (t.count) LCS_CK(ctx, cudaMemcpy(lens.data(), t.d_lens, sizeof(int64_t) * t.count, cudaMemcpyDeviceToHost));
     LCS_CK(ctx, cudaMemcpy(&err, t.d_err, sizeof(int), cudaMemcpyDeviceToHost));
     float ms = 0.0f;
-    LCS_CK(ctx, cudaEventElapsedTime(&ms, t.ev_start, t.ev_done));
+    LCS_CK(ctx, cudaEventElapsedTime(&ms, t.lane.ev_start, t.lane.ev_done));
     const lcs_status dev_status = (err & ERR_TIMEOUT) ? LCS_ETIMEOUT : (err ? LCS_ECUDA : LCS_OK);
     const int64_t nw = std::min(cap, t.count);
     for (int64_t q = 0; q < nw; ++q) {
@@ -1127,7 +1163,7 @@ lcs_status lcs_batch_strings(lcs_ctx *ctx, uint64_t ticket, uint8_t *out, int64_
     BatchTicket &t = it->second;
     *bytes = t.strings_bytes;
     LCS_CK(ctx, cudaSetDevice(ctx->device));
-    LCS_CK(ctx, cudaEventSynchronize(t.ev_done));
+    LCS_CK(ctx, cudaEventSynchronize(t.lane.ev_done));
     if (cap < t.strings_bytes) return fail(ctx, LCS_EOVERFLOW, "string buffer too small");
     if (t.strings_bytes > 0) {
         if (!out) return LCS_EINVAL;
@@ -1142,16 +1178,9 @@ lcs_status lcs_batch_release(lcs_ctx *ctx, uint64_t ticket) {
     if (it == ctx->tickets.end()) return fail(ctx, LCS_EINVAL, "unknown batch ticket");
     BatchTicket &t = it->second;
     LCS_CK(ctx, cudaSetDevice(ctx->device));
-    LCS_CK(ctx, cudaStreamSynchronize(t.stream));
-    cudaFree(t.dev);
-    cudaEventDestroy(t.ev_start);
-    cudaEventDestroy(t.ev_done);
-    cudaEventDestroy(t.ev_fork);
-    cudaStreamDestroy(t.stream);
-    for (int c = 0; c < kBatchClasses; ++c) {
-        cudaStreamDestroy(t.aux[c]);
-        cudaEventDestroy(t.ev_join[c]);
-    }
+    LCS_CK(ctx, cudaStreamSynchronize(t.lane.stream));
+    LCS_CK(ctx, cudaFreeAsync(t.dev, t.lane.stream));     // stream ordered: no device synchronisation
+    ctx->free_lanes.push_back(t.lane);
     ctx->batch_bytes -= t.bytes;
     ctx->tickets.erase(it);
     return LCS_OK;

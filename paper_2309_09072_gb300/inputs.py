@@ -16,6 +16,8 @@ The paper states neither the alphabet nor the distribution of its inputs
   different uniform letter with probability ``p_sub``; the result is truncated
   or padded with uniform letters to the requested length.
 * ``loguniform_lengths``: floor(exp(U(ln lo, ln (hi + 1)))) clipped to [lo, hi].
+* ``serving_requests``: Poisson arrivals (exponential gaps), every 50th pair
+  m = n = 16384, the others log-uniform in [128, 8192], 30% correlated.
 
 Seeds: ``numpy.random.default_rng(seed)``; ``a`` is drawn before ``b``.
 """
@@ -50,20 +52,20 @@ def mutate(rng: np.random.Generator, a: np.ndarray, p_sub: float, p_indel: float
     coin = rng.random(len(a))
     ins_letter = rng.integers(0, k, size=len(a))
     sub_shift = rng.integers(1, k, size=len(a))   # a *different* letter
-    pos_of = {int(c): i for i, c in enumerate(alphabet)}
-    out = []
-    for x in range(len(a)):
-        ch = int(a[x])
-        if u[x] < p_indel:
-            if coin[x] < 0.5:
-                out.append(int(alphabet[ins_letter[x]]))
-                out.append(ch)
-            # else: deletion, the letter is dropped
-        elif u[x] < p_indel + p_sub:
-            out.append(int(alphabet[(pos_of[ch] + sub_shift[x]) % k]))
-        else:
-            out.append(ch)
-    b = np.array(out, dtype=np.uint8)
+    pos_of = np.zeros(256, dtype=np.int64)
+    pos_of[np.asarray(alphabet, dtype=np.uint8)] = np.arange(k)
+    indel = u < p_indel
+    ins = indel & (coin < 0.5)                    # a uniform letter, then the position's
+    dele = indel & (coin >= 0.5)                  # the position's letter is dropped
+    sub = ~indel & (u < p_indel + p_sub)
+    letter = a.copy()
+    letter[sub] = np.asarray(alphabet, dtype=np.uint8)[(pos_of[a[sub]] + sub_shift[sub]) % k]
+    counts = 1 - dele.astype(np.int64) + ins.astype(np.int64)
+    start = np.cumsum(counts) - counts
+    b = np.empty(int(counts.sum()), dtype=np.uint8)
+    keep = counts > 0
+    b[start[keep] + ins[keep]] = letter[keep]
+    b[start[ins]] = np.asarray(alphabet, dtype=np.uint8)[ins_letter[ins]]
     if out_len is not None:
         if len(b) >= out_len:
             b = b[:out_len]
@@ -118,6 +120,33 @@ def batch_pairs(count: int = 20000, seed: int = 3, lo: int = 32, hi: int = 2048)
         b = uniform(rng, n, ACGT)
         pairs.append((a, b))
     return pairs
+
+
+def serving_requests(duration_s: float = 60.0, rate: float = 2000.0, seed: int = 4,
+                     lo: int = 128, hi: int = 8192, every_big: int = 50, big: int = 16384,
+                     p_correlated: float = 0.30):
+    """Poisson arrivals at ``rate`` pairs/s for ``duration_s`` seconds over the
+    20 letters (bytes 0..19, uniform): lengths log-uniform in [lo, hi], every
+    ``every_big``-th pair m = n = ``big``; a fraction ``p_correlated`` of the
+    pairs have b = a with 10% substitutions and 5% insertions/deletions.
+    Returns (arrival times in seconds, list of (a, b))."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=int(duration_s * rate * 1.2) + 16)
+    times = np.cumsum(gaps)
+    times = times[times < duration_s]
+    pairs = []
+    for k in range(len(times)):
+        if (k + 1) % every_big == 0:
+            m = n = big
+        else:
+            m, n = (int(x) for x in loguniform_lengths(rng, 2, lo, hi))
+        a = uniform(rng, m, AA20)
+        if rng.random() < p_correlated:
+            b = mutate(rng, a, 0.10, 0.05, AA20)
+        else:
+            b = uniform(rng, n, AA20)
+        pairs.append((a, b))
+    return times, pairs
 
 
 def random_pair(rng: np.random.Generator, m: int, n: int, alphabet: np.ndarray = ACGT):
