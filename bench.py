@@ -342,7 +342,6 @@ def run_ours(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    B.lcs_set_profiling(ctx, True)
     clocks = ClockSampler(local)
     barrier()
     for k in range(args.steps):
@@ -354,6 +353,15 @@ def run_ours(args):
     clock_info = clocks.stop()
     B.lcs_sync(ctx, stream)
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # Per-kernel times: a second pass of the same steps with an event pair
+    # around every launch (the events also stop consecutive kernels from
+    # overlapping their launches, so this pass is not the timed one).
+    prof_steps = min(args.steps, 50)
+    B.lcs_set_profiling(ctx, True)
+    for k in range(prof_steps):
+        flush.fill_(k & 0xFF)
+        step()
+    B.lcs_sync(ctx, stream)
     profile = B.lcs_get_profile(ctx)
     B.lcs_set_profiling(ctx, False)
     if world > 1:
@@ -394,6 +402,7 @@ def run_ours(args):
             "roofline": roofline(profile, peaks, peaks_src, int_peak),
             "clocks": clock_info,
             "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
+            "kernels_steps": prof_steps,
             "lcs_length": L, "workspace_bytes": stats["peak_workspace_bytes"]}
     B.lcs_destroy(ctx)
     if rank == 0 and not args.no_batched:

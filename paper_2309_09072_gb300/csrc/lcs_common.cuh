@@ -16,6 +16,8 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 namespace lcsg {
@@ -115,6 +117,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Programmatic dependent launch.  A kernel of the solve chain begins with
+// pdl_wait_and_release(): it waits until the kernel before it in the stream
+// has completed and its writes are visible (griddepcontrol.wait), then lets
+// the next kernel be scheduled (griddepcontrol.launch_dependents).  Launched
+// with launch_pdl, the next kernel's CTAs are placed while this one runs and
+// block in their own wait, which hides the launch gap between the two.
+// Without the launch attribute (or after a copy or an event) both
+// instructions do nothing and the stream orders the kernels as usual.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // Barrier among `count` threads (a multiple of 32) of the CTA on hardware

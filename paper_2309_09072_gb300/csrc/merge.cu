@@ -58,6 +58,7 @@ int64_t coarse_sigma0(int64_t P) {
 
 template <typename TIn>
 __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
+    pdl_wait_and_release();
     const int64_t P = p.P, n = p.n, sigma = p.sigma;
     const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);   // points 0, s, 2s, .., P
     const int64_t per_job = cnt * cnt;
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
 // point (threads over k, then a block-wide leftmost argmax).
 template <typename TIn>
 __global__ void __launch_bounds__(256) coarse_full_kernel(MergeParams p) {
+    pdl_wait_and_release();
     __shared__ int sv[8], sk[8];
     const int64_t P = p.P, n = p.n, sigma = p.sigma;
     const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);
@@ -157,12 +159,11 @@ cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
         const int64_t cnt = p.P / p.sigma + 1 + ((p.P % p.sigma) ? 1 : 0);
         const unsigned blocks = (unsigned)(cnt * cnt * p.njobs);
         switch (in_dtype) {
-            case DT_U8: coarse_full_kernel<uint8_t><<<blocks, 256, 0, st>>>(p); break;
-            case DT_I16: coarse_full_kernel<int16_t><<<blocks, 256, 0, st>>>(p); break;
-            case DT_I32: coarse_full_kernel<int32_t><<<blocks, 256, 0, st>>>(p); break;
+            case DT_U8: return launch_pdl(coarse_full_kernel<uint8_t>, dim3(blocks), dim3(256), 0, st, p);
+            case DT_I16: return launch_pdl(coarse_full_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, p);
+            case DT_I32: return launch_pdl(coarse_full_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, p);
             default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
     const int64_t cnt = p.P / p.sigma + 2;
     const int64_t warps = cnt * cnt * p.njobs;
@@ -170,9 +171,9 @@ cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     switch (in_dtype) {
-        case DT_U8: coarse_kernel<uint8_t><<<(unsigned)blocks, 256, 0, st>>>(p); break;
-        case DT_I16: coarse_kernel<int16_t><<<(unsigned)blocks, 256, 0, st>>>(p); break;
-        case DT_I32: coarse_kernel<int32_t><<<(unsigned)blocks, 256, 0, st>>>(p); break;
+        case DT_U8: return launch_pdl(coarse_kernel<uint8_t>, dim3((unsigned)blocks), dim3(256), 0, st, p);
+        case DT_I16: return launch_pdl(coarse_kernel<int16_t>, dim3((unsigned)blocks), dim3(256), 0, st, p);
+        case DT_I32: return launch_pdl(coarse_kernel<int32_t>, dim3((unsigned)blocks), dim3(256), 0, st, p);
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -440,6 +441,7 @@ __device__ __forceinline__ void refine_tile(const Operands<TIn, SMEM> op, int32_
 
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
+    pdl_wait_and_release();
     constexpr int PI = Fmt<TIn>::P, PO = Fmt<TOut>::P;
     constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
     constexpr int BUF = Band<TIn>::BUF;
@@ -637,8 +639,7 @@ static cudaError_t launch_tile_t(const MergeParams &p, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)num_tiles_tri(p.NT), (unsigned)p.njobs);
-    kern<<<grid, kTileThreads, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, dim3(kTileThreads), smem, st, p);
 }
 
 cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaStream_t st) {
@@ -703,6 +704,7 @@ struct DpxMeta {
 
 template <typename TOut>
 __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
+    pdl_wait_and_release();
     using TIn = int16_t;
     constexpr int PI = Fmt<TIn>::P, PO = Fmt<TOut>::P;
     constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
@@ -958,8 +960,7 @@ static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDpxThreads, smem)) != cudaSuccess) return e;
     const int64_t work = p.njobs * num_tiles_tri(p.NT);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
-    kern<<<(unsigned)grid, kDpxThreads, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3((unsigned)grid), dim3(kDpxThreads), smem, st, p);
 }
 
 cudaError_t launch_tile_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
@@ -1000,6 +1001,7 @@ cudaError_t launch_tile_pair(MergeParams p, int in_dtype, int out_dtype, cudaStr
 template <typename V>
 __global__ void __launch_bounds__(256) pack_kernel(const V *src, int64_t ld, int64_t n, int64_t NT,
                                                    V *dst, int layout) {
+    pdl_wait_and_release();
     constexpr int P = Fmt<V>::P, E = Fmt<V>::ELEMS;
     __shared__ V tile[T][T + 1];
     const int64_t tix = blockIdx.x;
@@ -1029,9 +1031,11 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int64_t ld, void 
     const int64_t NT = num_tiles_side(n);
     const unsigned blocks = (unsigned)num_tiles_tri(NT);
     if (dtype == DT_I32)
-        pack_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t *)src, ld, n, NT, (int32_t *)dst, layout);
+        return launch_pdl(pack_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, (const int32_t *)src, ld, n, NT,
+                          (int32_t *)dst, layout);
     else if (dtype == DT_I16)
-        pack_kernel<int16_t><<<blocks, 256, 0, st>>>((const int16_t *)src, ld, n, NT, (int16_t *)dst, layout);
+        return launch_pdl(pack_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, (const int16_t *)src, ld, n, NT,
+                          (int16_t *)dst, layout);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -1041,6 +1045,7 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int64_t ld, void 
 template <typename V>
 __global__ void fill_dense_kernel(V *out, int64_t n, int64_t ld, V lower, V upper, int fill_upper,
                                   int32_t *K) {
+    pdl_wait_and_release();
     for (int64_t i = blockIdx.x; i <= n; i += gridDim.x) {
         // Lower triangle outside the diagonal tile: columns [0, (i/T)*T).
         const int64_t jl = fill_upper ? i : ((i >> T_SHIFT) << T_SHIFT);
@@ -1057,14 +1062,12 @@ cudaError_t launch_fill_dense(void *out, int dtype, int64_t n, int64_t ld, int l
                               int fill_upper, int32_t *K, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 1) < 8192 ? (n + 1) : 8192);
     if (dtype == DT_I32)
-        fill_dense_kernel<int32_t><<<blocks, 256, 0, st>>>((int32_t *)out, n, ld, (int32_t)lower,
-                                                           (int32_t)upper, fill_upper, K);
-    else if (dtype == DT_I16)
-        fill_dense_kernel<int16_t><<<blocks, 256, 0, st>>>((int16_t *)out, n, ld, (int16_t)lower,
-                                                           (int16_t)upper, fill_upper, K);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_pdl(fill_dense_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, (int32_t *)out, n, ld,
+                          (int32_t)lower, (int32_t)upper, fill_upper, K);
+    if (dtype == DT_I16)
+        return launch_pdl(fill_dense_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, (int16_t *)out, n, ld,
+                          (int16_t)lower, (int16_t)upper, fill_upper, K);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lcsg

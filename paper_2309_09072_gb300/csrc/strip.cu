@@ -133,6 +133,7 @@ __device__ __forceinline__ void write_tile_part(const StripParams &p, OutT *out,
 
 template <typename OutT, int W>
 __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) {
+    pdl_wait_and_release();
     constexpr int P = StagePitch<OutT>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *masks = reinterpret_cast<uint32_t *>(smem);             // [256][W]
@@ -252,8 +253,7 @@ static cudaError_t launch_t(const StripParams &p, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const int64_t bands = p.NT - p.band_first;
     dim3 grid((unsigned)ceil_div(bands, kStripBands), (unsigned)p.S);
-    kern<<<grid, kStripWarps * 32, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, dim3(kStripWarps * 32), smem, st, p);
 }
 
 template <typename OutT>

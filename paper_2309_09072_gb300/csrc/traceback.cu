@@ -20,6 +20,7 @@ namespace lcsg {
 
 // ------------------------------------------------------------------ per-level argmax
 __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
+    pdl_wait_and_release();
     __shared__ int sv[8];
     __shared__ int64_t sk[8];
     const TbMerge mg = p.merges[blockIdx.x];
@@ -57,19 +58,18 @@ __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
 }
 
 __global__ void root_path_kernel(int32_t *pI, int32_t *pJ, int32_t root, int32_t n) {
+    pdl_wait_and_release();
     pI[root] = 0;
     pJ[root] = n;
 }
 
 cudaError_t launch_root_path(int32_t *pathI, int32_t *pathJ, int32_t root, int64_t n, cudaStream_t st) {
-    root_path_kernel<<<1, 1, 0, st>>>(pathI, pathJ, root, (int32_t)n);
-    return cudaGetLastError();
+    return launch_pdl(root_path_kernel, dim3(1), dim3(1), 0, st, pathI, pathJ, root, (int32_t)n);
 }
 
 cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st) {
     if (p.count <= 0) return cudaSuccess;
-    tb_level_kernel<<<(unsigned)p.count, 256, 0, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(tb_level_kernel, dim3((unsigned)p.count), dim3(256), 0, st, p);
 }
 
 // ------------------------------------------------------------------ leaves
@@ -204,6 +204,7 @@ __device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0
 // into row r marks letter a_r (Sec. II-E).
 template <int W>
 __global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
+    pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem + warp * leaf_warp_bytes(W));   // [256][W] match masks
@@ -248,8 +249,7 @@ static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
     auto kern = leaf_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)ceil_div(p.S, kLeafWarps), kLeafWarps * 32, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3((unsigned)ceil_div(p.S, kLeafWarps)), dim3(kLeafWarps * 32), smem, st, p);
 }
 
 cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st) {
@@ -265,6 +265,7 @@ cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st) {
 
 // ------------------------------------------------------------------ compaction
 __global__ void __launch_bounds__(1024) compact_kernel(CompactParams p, int32_t *offsets) {
+    pdl_wait_and_release();
     __shared__ int32_t warp_sums[32];
     __shared__ int32_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -313,8 +314,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(CompactParams p, int32_t 
 
 cudaError_t launch_compact(const CompactParams &p, cudaStream_t st) {
     // offsets live right after the counts array (the planner reserves 2*S ints).
-    compact_kernel<<<1, 1024, 0, st>>>(p, const_cast<int32_t *>(p.counts) + p.S);
-    return cudaGetLastError();
+    return launch_pdl(compact_kernel, dim3(1), dim3(1024), 0, st, p, const_cast<int32_t *>(p.counts) + p.S);
 }
 
 cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st) {
