@@ -120,6 +120,22 @@ const char *lcs_last_error(lcs_ctx *ctx);
  * Errors: EINVAL. */
 lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
 
+/* Kernel that computes the tree's merge tiles (Sec. II-B-3: every entry of
+ * D(i, j) = max_k U(i, k) + L(k, j)).  Both give the same D, so the choice
+ * changes speed only.
+ *   LCS_MERGE_AUTO   LCS_MERGE_DPX when every merge operand of the tree
+ *                    fits int16 values <= 16383 (strips of <= 16383 rows
+ *                    below the root), else LCS_MERGE_EXACT.
+ *   LCS_MERGE_EXACT  Monge-windowed refinement of each 64 x 64 tile from
+ *                    its corner maximisers, with the exact leftmost argmax.
+ *   LCS_MERGE_DPX    (max,+) product of each tile over the band between its
+ *                    corner maximisers on DPX instructions (D only); where
+ *                    the operands do not fit int16, EXACT is used.
+ * Applies to lcs_solve* and lcs_dist* on this ctx; lcs_merge, which returns
+ * the argmax, always refines exactly.  Errors: EINVAL. */
+enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2 };
+lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
+
 /* Counters of the last call (see lcs_stats).  Errors: EINVAL. */
 lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out);
 

@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
             "lcs_strerror": ([st], ctypes.c_char_p),
             "lcs_last_error": ([vp], ctypes.c_char_p),
             "lcs_set_strip_height": ([vp, i32], st),
+            "lcs_set_merge_kernel": ([vp, i32], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
             "lcs_sync": ([vp, vp], st),
             "lcs_set_profiling": ([vp, i32], st),
@@ -201,6 +202,13 @@ def lcs_last_error(ctx) -> str:
 
 def lcs_set_strip_height(ctx, h: int) -> None:
     _check(ctx, load().lcs_set_strip_height(ctx, int(h)))
+
+
+LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX = 0, 1, 2
+
+
+def lcs_set_merge_kernel(ctx, kind: int) -> None:
+    _check(ctx, load().lcs_set_merge_kernel(ctx, int(kind)))
 
 
 def lcs_get_stats(ctx) -> dict:

@@ -144,6 +144,7 @@ struct lcs_ctx {
     int device = 0;
     size_t budget = 0;
     int32_t strip_h = 0;
+    int32_t merge_kernel = LCS_MERGE_AUTO;
     char *ws = nullptr;          // plan workspace
     size_t ws_bytes = 0;
     char *io = nullptr;          // host-call staging (lcs_solve_host, lcs_merge)
@@ -605,7 +606,8 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 mp.sigma = (int32_t)sg; mp.full = 0;
                 LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             }
-            if (P.dpx) {
+            const int mk = ctx->merge_kernel;
+            if (P.dpx && mk != LCS_MERGE_EXACT) {
                 LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
                             0.0, launch_tile_dpx(mp, g.out_dt, st));
             } else {
@@ -733,6 +735,12 @@ const char *lcs_last_error(lcs_ctx *ctx) { return ctx ? ctx->last_error.c_str() 
 lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
     if (!ctx || h < 0 || h > 256) return fail(ctx, LCS_EINVAL, "strip height must be 0..256");
     ctx->strip_h = h;
+    return LCS_OK;
+}
+
+lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
+    if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
+    ctx->merge_kernel = kind;
     return LCS_OK;
 }
 
