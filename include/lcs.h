@@ -230,6 +230,19 @@ lcs_status lcs_length(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *
 lcs_status lcs_traceback(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                          uint8_t *out_lcs, int64_t cap, int64_t *out_len_host, void *stream);
 
+/* The leftmost heaviest path itself, as the list of its grid vertices
+ * (Sec. II-D: each row's horizontal run between consecutive cross vertices,
+ * the runs placed in row order by a prefix sum).  Vertex (r, c) is the
+ * grid point after r letters of a and c letters of b; the list runs from
+ * (0, 0) to (m, n) and has m + n + 1 - L entries (a match diagonal enters
+ * a row one column right of where the previous row's run ended).
+ * path: device int32 array of 2 * cap entries receiving (row, col) pairs.
+ * Synchronises the stream and writes *out_count_host (the vertex count).
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT; EOVERFLOW when cap is below the
+ * vertex count (nothing written to path, *out_count_host untouched). */
+lcs_status lcs_path(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    int32_t *path, int64_t cap, int64_t *out_count_host, void *stream);
+
 /* The whole hot path in one call: strips, merge tree, and any of
  *   dist  (nullable): dense (n+1) x ld DIST in dtype;
  *   out_lcs (nullable): the LCS letters (cap >= min(m, n) bytes);

@@ -62,6 +62,8 @@ def _load():
             lib.oracle_merge.restype = None
             lib.oracle_traceback.argtypes = [u8p, i64, u8p, i64, u8p, i64p]
             lib.oracle_traceback.restype = i64
+            lib.oracle_path.argtypes = [u8p, i64, u8p, i64, i64p, i64p]
+            lib.oracle_path.restype = i64
             lib.oracle_dform.argtypes = [i32p, i64, i64, i64, i64p]
             lib.oracle_dform.restype = None
             lib.oracle_leaf_dform.argtypes = [ctypes.c_uint8, u8p, i64, i64p, i64p]
@@ -150,6 +152,19 @@ def traceback(a, b):
     if r < 0:
         raise MemoryError("oracle_traceback")
     return bytes(out[:r]), v
+
+
+def path(a, b) -> np.ndarray:
+    """Vertices (row, col) of the leftmost heaviest path, (0, 0) to (m, n)."""
+    a, b = _u8(a), _u8(b)
+    m, n = len(a), len(b)
+    rows = np.zeros(m + n + 1, dtype=np.int64)
+    cols = np.zeros(m + n + 1, dtype=np.int64)
+    r = _load().oracle_path(_p(a, ctypes.c_uint8), m, _p(b, ctypes.c_uint8), n,
+                            _p(rows, ctypes.c_int64), _p(cols, ctypes.c_int64))
+    if r < 0:
+        raise MemoryError("oracle_path")
+    return np.stack([rows[:r], cols[:r]], axis=1)
 
 
 def dform(D: np.ndarray, wmax: int) -> np.ndarray:

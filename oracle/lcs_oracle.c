@@ -196,8 +196,8 @@ void oracle_merge(const int32_t *U, const int32_t *L, int64_t n, int64_t ld,
  * Returns L (the number of letters written to out), or -1 on error.
  * v (nullable) receives v[0..m].
  * ---------------------------------------------------------------------- */
-int64_t oracle_traceback(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
-                         uint8_t *out, int64_t *v)
+static int64_t leftmost_path(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                             uint8_t *out, int64_t *v, uint8_t *gain)
 {
     int64_t W = n + 1;
     int32_t *Bt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1) * (size_t)W);
@@ -215,6 +215,7 @@ int64_t oracle_traceback(const uint8_t *a, int64_t m, const uint8_t *b, int64_t 
     int32_t L = Bt[0];
     int64_t vprev = 0;                 /* F(0, c) = 0 and B(0, 0) = L, so v[0] = 0 */
     if (v) v[0] = 0;
+    if (gain) gain[0] = 0;
     int64_t len = 0;
     for (int64_t r = 1; r <= m; ++r) {
         Fc[0] = 0;
@@ -227,7 +228,9 @@ int64_t oracle_traceback(const uint8_t *a, int64_t m, const uint8_t *b, int64_t 
             if (Fc[c] + Bt[r * W + c] == L) { vr = c; break; }
         }
         if (vr < 0) { len = -1; break; }
-        if (Fc[vr] - Fp[vprev] == 1) {
+        const int g = Fc[vr] - Fp[vprev] == 1;
+        if (gain) gain[r] = (uint8_t)g;
+        if (g) {
             if (out) out[len] = a[r - 1];
             ++len;
         }
@@ -237,6 +240,44 @@ int64_t oracle_traceback(const uint8_t *a, int64_t m, const uint8_t *b, int64_t 
     }
     free(Bt); free(Fp); free(Fc);
     return len;
+}
+
+int64_t oracle_traceback(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                         uint8_t *out, int64_t *v)
+{
+    return leftmost_path(a, m, b, n, out, v, NULL);
+}
+
+/* ------------------------------------------------------------------------
+ * The vertex list of the same leftmost heaviest path (Sec. II-D): in row r
+ * the path runs right from its cross vertex v[r] to the column where it
+ * leaves the row, then steps down into row r+1 at v[r+1].  The step gains
+ * weight 1 (F(r+1, v[r+1]) - F(r, v[r]) = 1) only on a match diagonal, which
+ * leaves row r at column v[r+1] - 1; otherwise it is vertical and leaves at
+ * v[r+1].  The last row runs to column n.  The runs are concatenated in row
+ * order.  rows/cols (capacity m + n + 1 each) receive the vertices from
+ * (0, 0) to (m, n).  Returns the vertex count, or -1 on error.
+ * ---------------------------------------------------------------------- */
+int64_t oracle_path(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    int64_t *rows, int64_t *cols)
+{
+    int64_t *v = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    uint8_t *gain = (uint8_t *)malloc((size_t)m + 1);
+    if (!v || !gain) { free(v); free(gain); return -1; }
+    int64_t cnt = -1;
+    if (leftmost_path(a, m, b, n, NULL, v, gain) >= 0) {
+        cnt = 0;
+        for (int64_t r = 0; r <= m; ++r) {
+            const int64_t end = (r == m) ? n : (gain[r + 1] ? v[r + 1] - 1 : v[r + 1]);
+            for (int64_t c = v[r]; c <= end; ++c) {
+                rows[cnt] = r;
+                cols[cnt] = c;
+                ++cnt;
+            }
+        }
+    }
+    free(v); free(gain);
+    return cnt;
 }
 
 /* ------------------------------------------------------------------------

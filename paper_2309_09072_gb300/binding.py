@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
             "lcs_dist": ([vp, vp, i64, vp, i64, st, vp, i64, vp], st),
             "lcs_length": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_traceback": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+            "lcs_path": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_solve": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, vp, vp, vp], st),
             "lcs_solve_host": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_batch_submit": ([vp, ctypes.POINTER(lcs_pair), i64, ctypes.POINTER(ctypes.c_uint64)], st),
@@ -282,6 +283,16 @@ def lcs_traceback(ctx, a, b, out_lcs, stream=None) -> int:
     out = ctypes.c_int64()
     _check(ctx, load().lcs_traceback(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(out_lcs),
                                      int(out_lcs.numel()), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def lcs_path(ctx, a, b, path, stream=None) -> int:
+    """Vertices of the leftmost heaviest path into ``path`` (int32, shape
+    (cap, 2) of (row, col) pairs); returns their number."""
+    out = ctypes.c_int64()
+    cap = int(path.numel()) // 2 if path is not None else 0
+    _check(ctx, load().lcs_path(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(path), cap,
+                                ctypes.byref(out), _stream(stream)))
     return out.value
 
 

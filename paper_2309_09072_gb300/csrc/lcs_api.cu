@@ -909,6 +909,35 @@ lcs_status lcs_traceback(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_
     return read_back(ctx, st, out_len_host);
 }
 
+lcs_status lcs_path(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    int32_t *path, int64_t cap, int64_t *out_count_host, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    if (!out_count_host) return fail(ctx, LCS_EINVAL, "out_count_host is NULL");
+    if (cap < 0 || (cap > 0 && !path)) return fail(ctx, LCS_EINVAL, "path is NULL or cap < 0");
+    if (m < 0 || n < 0 || m >= INT32_MAX / 2 || n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "length");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // Staging: cross vertices, run offsets, the vertex count.
+    const size_t rows_b = align256((size_t)(m + 1) * sizeof(int32_t));
+    lcs_status s = ensure_io(ctx, 2 * rows_b + 256);
+    if (s != LCS_OK) return s;
+    int32_t *cross = reinterpret_cast<int32_t *>(ctx->io);
+    int32_t *offs = reinterpret_cast<int32_t *>(ctx->io + rows_b);
+    int64_t *cnt = reinterpret_cast<int64_t *>(ctx->io + 2 * rows_b);
+    s = solve_device(ctx, a, m, b, n, LCS_I32, nullptr, 0, nullptr, 0, cross, nullptr, true, st);
+    if (s != LCS_OK) return s;
+    PathParams pp{};
+    pp.a = a; pp.b = b; pp.m = m; pp.n = n; pp.cross = cross; pp.offsets = offs;
+    pp.path = path; pp.cap = cap; pp.len = len_word(ctx); pp.count_out = cnt; pp.err = err_word(ctx);
+    LCS_LAUNCHK(ctx, st, K_COMPACT, 0.0, 0.0, launch_path(pp, st));
+    ctx->stats.kernel_launches = ctx->launches;
+    int64_t len = 0;
+    s = read_back(ctx, st, &len);
+    if (s != LCS_OK) return s;
+    *out_count_host = m + n + 1 - len;
+    return LCS_OK;
+}
+
 lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const uint8_t *b_host, int64_t n,
                           lcs_dtype dtype, void *dist_host, int64_t ld, uint8_t *lcs_host, int64_t cap,
                           int64_t *out_len_host, void *stream) {

@@ -168,6 +168,21 @@ struct CompactParams {
 };
 cudaError_t launch_compact(const CompactParams &p, cudaStream_t st);
 
+// Vertex list of the leftmost heaviest path from the cross vertices
+// (traceback.cu): one CTA scans the rows' run lengths and writes the runs.
+struct PathParams {
+    const uint8_t *a, *b;
+    int64_t m, n;
+    const int32_t *cross;  // v[0..m]
+    int32_t *offsets;      // m + 1 ints of scratch
+    int32_t *path;         // 2 * cap ints: (row, col) pairs
+    int64_t cap;
+    const int64_t *len;    // device word holding the LCS length
+    int64_t *count_out;    // device word receiving the vertex count
+    int *err;
+};
+cudaError_t launch_path(const PathParams &p, cudaStream_t st);
+
 // Copy the internal length word to the caller's word (device to device).
 cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st);
 

@@ -317,6 +317,100 @@ cudaError_t launch_compact(const CompactParams &p, cudaStream_t st) {
     return launch_pdl(compact_kernel, dim3(1), dim3(1024), 0, st, p, const_cast<int32_t *>(p.counts) + p.S);
 }
 
+// ------------------------------------------------------------------ path listing
+// The leftmost heaviest path as a vertex list (Sec. II-D: the horizontal
+// runs between consecutive cross vertices, placed by a prefix sum).  Row r's
+// run starts at its cross vertex v[r] and ends where the path steps down.
+// The step into row r+1 lands on v[r+1]; it is a match diagonal exactly
+// when v[r+1] > v[r] and a_{r+1} = b_{v[r+1]} (a vertical step at a column
+// where the diagonal into it matches would give up one unit of weight, so a
+// heaviest path never takes it), and then the run ends at v[r+1] - 1; else
+// at v[r+1].  The last row runs to n.  The vertex count is m + n + 1 - L.
+__device__ __forceinline__ int64_t path_run(const PathParams &p, int64_t r, bool &bad) {
+    const int64_t v0 = p.cross[r];
+    if (v0 < 0 || v0 > p.n) {
+        bad = true;
+        return 1;
+    }
+    int64_t e = p.n;
+    if (r < p.m) {
+        const int64_t v1 = p.cross[r + 1];
+        if (v1 < v0 || v1 > p.n) {
+            bad = true;
+            return 1;
+        }
+        e = (v1 > v0 && p.a[r] == p.b[v1 - 1]) ? v1 - 1 : v1;
+    }
+    if (v0 > e) {
+        bad = true;
+        return 1;
+    }
+    return e - v0 + 1;
+}
+
+__global__ void __launch_bounds__(1024) path_kernel(PathParams p) {
+    pdl_wait_and_release();
+    __shared__ int32_t warp_sums[32];
+    __shared__ int64_t carry;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rows = p.m + 1;
+    for (int64_t base = 0; base < rows; base += 1024) {
+        const int64_t r = base + threadIdx.x;
+        bool bad = false;
+        const int32_t v = r < rows ? (int32_t)path_run(p, r, bad) : 0;
+        if (bad) s_bad = 1;
+        int32_t x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = warp_sums[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+                if (lane >= off) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int32_t incl = x + (warp > 0 ? warp_sums[warp - 1] : 0);
+        if (r < rows) p.offsets[r] = (int32_t)carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    const int64_t total = carry;
+    const int64_t want = p.m + p.n + 1 - *p.len;
+    if (threadIdx.x == 0) {
+        if (p.count_out) *p.count_out = total;
+        if (s_bad || total != want) set_error(p.err, ERR_BOUNDS);
+        else if (total > p.cap) set_error(p.err, ERR_OVERFLOW);
+    }
+    if (s_bad || total != want || total > p.cap) return;
+    for (int64_t r = warp; r < rows; r += 32) {
+        bool bad = false;
+        const int64_t len = path_run(p, r, bad), off = p.offsets[r], v0 = p.cross[r];
+        for (int64_t t = lane; t < len; t += 32) {
+            p.path[2 * (off + t)] = (int32_t)r;
+            p.path[2 * (off + t) + 1] = (int32_t)(v0 + t);
+        }
+    }
+}
+
+cudaError_t launch_path(const PathParams &p, cudaStream_t st) {
+    return launch_pdl(path_kernel, dim3(1), dim3(1024), 0, st, p);
+}
+
 cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st) {
     return cudaMemcpyAsync(dst, src, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
 }

@@ -315,6 +315,78 @@ def _tree_traceback(a, b, split):
     return v, out
 
 
+def heaviest_vertex_paths(a, b):
+    """Every heaviest source->sink path as its full vertex list, by
+    exhaustive depth-first enumeration of all lattice paths (tiny inputs)."""
+    m, n = len(a), len(b)
+    found = []
+
+    def walk(r, c, w, verts):
+        if r == m and c == n:
+            found.append((w, tuple(verts)))
+            return
+        if c < n:
+            walk(r, c + 1, w, verts + [(r, c + 1)])
+        if r < m:
+            walk(r + 1, c, w, verts + [(r + 1, c)])
+        if r < m and c < n and a[r] == b[c]:
+            walk(r + 1, c + 1, w + 1, verts + [(r + 1, c + 1)])
+
+    walk(0, 0, 0, [(0, 0)])
+    top = max(w for w, _ in found)
+    return top, [p for w, p in found if w == top]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_path_listing_is_leftmost_heaviest_path(seed):
+    """Sec. II-D: the listed vertices form the heaviest path whose run in
+    every row starts and ends at the smallest columns any heaviest path uses
+    there (found by enumerating every lattice path of tiny grids)."""
+    for a, b in small_pairs(700 + seed, 20, 0, 6, b"ACG"):
+        m, n = len(a), len(b)
+        total, paths = heaviest_vertex_paths(a, b)
+
+        def runs(p):
+            first, last = {}, {}
+            for r, c in p:
+                first.setdefault(r, c)
+                last[r] = c
+            return tuple((first[r], last[r]) for r in range(m + 1))
+
+        lo = tuple((min(runs(p)[r][0] for p in paths), min(runs(p)[r][1] for p in paths)) for r in range(m + 1))
+        leftmost = [p for p in paths if runs(p) == lo]
+        assert len(leftmost) == 1
+        got = oracle.path(a, b)
+        assert [tuple(int(x) for x in v) for v in got] == list(leftmost[0])
+        assert len(got) == m + n + 1 - total
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_path_listing_invariants(seed):
+    """Larger pairs: the path starts at (0, 0), ends at (m, n), every step is
+    right, down or a match diagonal, the diagonals spell the oracle's LCS and
+    their number is the exact length."""
+    rng = np.random.default_rng(800 + seed)
+    for m, n in [(1, 40), (40, 1), (90, 120), (150, 70)]:
+        a, b = inputs.random_pair(rng, m, n, np.frombuffer(b"AC" if seed % 2 else b"ACGT", np.uint8))
+        P = oracle.path(a, b)
+        s, v = oracle.traceback(a, b)
+        L = brute_lcs_len(a, b) if min(m, n) <= 12 else oracle.lcs_length(a, b)
+        assert tuple(P[0]) == (0, 0) and tuple(P[-1]) == (m, n)
+        assert len(P) == m + n + 1 - L
+        d = np.diff(P, axis=0)
+        steps = {tuple(x) for x in d}
+        assert steps <= {(0, 1), (1, 0), (1, 1)}
+        diag = np.flatnonzero((d[:, 0] == 1) & (d[:, 1] == 1))
+        assert all(a[P[k + 1][0] - 1] == b[P[k + 1][1] - 1] for k in diag)
+        assert bytes(a[P[k + 1][0] - 1] for k in diag) == s
+        # the first vertex of each row is its cross vertex
+        first = {}
+        for r, c in P:
+            first.setdefault(int(r), int(c))
+        assert [first[r] for r in range(m + 1)] == [int(x) for x in v]
+
+
 @pytest.mark.parametrize("rule", ["mid", "first", "last"])
 def test_traceback_tree_independent(rule):
     split = {"mid": lambda r0, r1: (r0 + r1) // 2,
