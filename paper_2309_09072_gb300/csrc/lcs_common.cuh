@@ -196,4 +196,76 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// ------------------------------------------------------------------ bit-vector step
+// s = x + y over W words; returns the carry out of the top word.
+template <int W> struct AddChain;
+template <> struct AddChain<1> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[1], const uint32_t (&x)[1],
+                                                   const uint32_t (&y)[1]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, 0, 0;" : "=r"(s[0]), "=r"(c) : "r"(x[0]), "r"(y[0]));
+        return c;
+    }
+};
+template <> struct AddChain<2> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[2], const uint32_t (&x)[2],
+                                                   const uint32_t (&y)[2]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %3, %5;\n\t"
+            "addc.cc.u32 %1, %4, %6;\n\t"
+            "addc.u32 %2, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(y[0]), "r"(y[1]));
+        return c;
+    }
+};
+template <> struct AddChain<4> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[4], const uint32_t (&x)[4],
+                                                   const uint32_t (&y)[4]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %5, %9;\n\t"
+            "addc.cc.u32 %1, %6, %10;\n\t"
+            "addc.cc.u32 %2, %7, %11;\n\t"
+            "addc.cc.u32 %3, %8, %12;\n\t"
+            "addc.u32 %4, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]));
+        return c;
+    }
+};
+template <> struct AddChain<8> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[8], const uint32_t (&x)[8],
+                                                   const uint32_t (&y)[8]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %9, %17;\n\t"
+            "addc.cc.u32 %1, %10, %18;\n\t"
+            "addc.cc.u32 %2, %11, %19;\n\t"
+            "addc.cc.u32 %3, %12, %20;\n\t"
+            "addc.cc.u32 %4, %13, %21;\n\t"
+            "addc.cc.u32 %5, %14, %22;\n\t"
+            "addc.cc.u32 %6, %15, %23;\n\t"
+            "addc.cc.u32 %7, %16, %24;\n\t"
+            "addc.u32 %8, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]),
+              "=r"(s[7]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]),
+              "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]), "r"(y[7]));
+        return c;
+    }
+};
+
+// One bit-vector column step (u = V & M, V' = (V + u) | (V & ~M), the
+// Allison-Dix / Hyyro step restated) for one source; returns the carry out
+// of the top row, the increment of DIST.
+template <int W>
+__device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t (&M)[W]) {
+    uint32_t u[W], s[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
+    uint32_t c = AddChain<W>::run(s, V, u);
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = s[w] | (V[w] & ~M[w]);
+    return c;
+}
+
 }  // namespace lcsg

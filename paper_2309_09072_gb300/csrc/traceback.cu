@@ -73,72 +73,127 @@ cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ leaves
-constexpr int kLeafWarps = 2;
-constexpr int kLeafSmemCols = 1024;   // forward bit-vectors kept in shared memory
+// One CTA per strip, whose part of the path runs from (0, i) to (hs, j).
+// With F(r, c) = LCS(a_strip[0:r], b[i:c]) (forward from the source) and
+// B(r, c) = LCS(a_strip[r:hs], b[c:j]) (backward from the sink), the
+// vertices on heaviest paths are those with F + B = L = F(hs, j), so the
+// leftmost heaviest path enters row r at
+//     v[r] = min{ c in [i, j] : F(r, c) + B(r, c) = L }     (Sec. II-C),
+// and the step into row r is a match diagonal, marking letter a_r
+// (Sec. II-E), exactly when v[r] > v[r-1] and a_r = b_{v[r]} (a vertical
+// step where the diagonal into the same vertex matches would give up one
+// unit of weight).  Warp 0 sweeps the columns forward and warp 1 backward
+// (the reversed strip against the reversed segment of b), both with the
+// bit-vector step of the strip builder, storing every column's vector; then
+// all warps test F + B = L for a slice of the columns, a lane per group of
+// rows, and the first hit of each row is its cross vertex.
+constexpr int kLeafThreads = 256;
+constexpr int kLeafSmemCols = 1024;   // columns whose vectors fit shared memory
 
-// Shared memory of one leaf warp: match masks, column vectors, the strip's
-// letters and b's segment.
-__host__ __device__ constexpr size_t leaf_warp_bytes(int W) {
-    return ((size_t)(256 * W + kLeafSmemCols * W) * 4 + (size_t)kLeafSmemCols * (W + 1) * 2 + 256 +
-            kLeafSmemCols + 15) / 16 * 16;
+struct LeafSmem {
+    size_t fm, fmr, vf, vb, vr, vmin, wsum, sa, sb, total;
+};
+__host__ __device__ constexpr LeafSmem leaf_smem_layout(int W) {
+    LeafSmem L{};
+    size_t off = 0;
+    L.fm = off;   off += (size_t)256 * W * 4;                      // forward row masks per letter
+    L.fmr = off;  off += (size_t)256 * W * 4;                      // the same over reversed rows
+    L.vf = off;   off += (size_t)(kLeafSmemCols + 1) * W * 4;      // forward column vectors
+    L.vb = off;   off += (size_t)(kLeafSmemCols + 1) * W * 4;      // backward column vectors
+    L.vr = off;   off += (size_t)(kLeafSmemCols + 1) * W * 4;      // backward ones, in forward row order
+    L.vmin = off; off += (size_t)(256 + 1) * 4;                    // cross vertex per row
+    L.wsum = off; off += 16 * 4;                                   // scan of the marks
+    L.sa = off;   off += 256;                                      // the strip's letters
+    L.sb = off;   off += kLeafSmemCols;                            // b[i .. j - 1]
+    L.total = (off + 15) / 16 * 16;
+    return L;
 }
 
-// F(r, c) of a strip = zeros among the first r bits of its column vector V_c
-// (a zero bit marks a row where the DP steps up).
+// Ones among the first `bits` bits of a W-word vector.
 template <int W>
-__device__ __forceinline__ int f_at(const uint32_t *v, int r) {
+__device__ __forceinline__ int prefix_ones(const uint32_t (&v)[W], int bits) {
     int ones = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        const int bits = min(max(r - 32 * w, 0), 32);          // of word w, the first `bits` rows
-        const uint32_t mask = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+        const int k = min(max(bits - 32 * w, 0), 32);
+        const uint32_t mask = k == 32 ? 0xFFFFFFFFu : ((1u << k) - 1u);
         ones += __popc(v[w] & mask);
     }
-    return r - ones;
+    return ones;
 }
 
-// Forward sweep and backward walk of one strip whose path runs from (0, i)
-// to (hs, j): column vectors in vb and b's segment in sb (shared memory,
-// kSmem) or vb in the global scratch and b read from global memory.
-template <int W, bool kSmem>
-__device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0, int hs, int64_t i, int64_t j,
-                                          const uint32_t *fm, uint32_t *vb, uint16_t *pp, const uint8_t *sa,
-                                          const uint8_t *sb, int lane) {
-    auto bch = [&](int64_t c) -> uint8_t {
-        if constexpr (kSmem) return sb[c - 1 - i];
-        else return p.b[c - 1];
-    };
-    // Forward sweep (every lane computes V; lane w stores word w).
-    // With the column vectors in shared memory, lane w <= W also stores the
-    // ones in the words below w, so that the walk's F(r, c) is one table
-    // entry plus one masked popcount.
+// W words to shared memory with the widest stores their alignment allows
+// (a column's vector starts on a 4 W-byte boundary).
+template <int W>
+__device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t (&v)[W]) {
+    if constexpr (W >= 4) {
+#pragma unroll
+        for (int w = 0; w < W; w += 4)
+            *reinterpret_cast<uint4 *>(dst + w) = make_uint4(v[w], v[w + 1], v[w + 2], v[w + 3]);
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
+    } else {
+        dst[0] = v[0];
+    }
+}
+
+// Sweep of `ncol` columns from the all-ones vector; column c (1-based) uses
+// the masks of letter seg[rev ? ncol - c : c - 1].  Every lane steps the
+// whole vector (one add-with-carry chain per column, no cross-lane traffic
+// on the dependent path), and every column's
+// vector, column 0 included (lane 0 writes it).  The letter and its masks
+// are fetched two and one columns ahead.
+template <int W>
+__device__ __forceinline__ void leaf_sweep(const uint32_t *masks, const uint8_t *seg, int ncol, bool rev,
+                                           uint32_t *out, int lane) {
+    uint32_t V[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
+    if (lane == 0) store_words<W>(out, V);
+    auto letter = [&](int c) -> int { return seg[rev ? ncol - c : c - 1]; };   // 1 <= c <= ncol
+    uint32_t M[W];
+    int chn = 0;
+    if (ncol > 0) {
+        const uint32_t *m0 = masks + letter(1) * W;
+#pragma unroll
+        for (int w = 0; w < W; ++w) M[w] = m0[w];
+        chn = letter(ncol > 1 ? 2 : 1);
+    }
+    for (int c = 1; c <= ncol; ++c) {
+        uint32_t Mn[W];
+        const uint32_t *mn = masks + chn * W;
+#pragma unroll
+        for (int w = 0; w < W; ++w) Mn[w] = mn[w];
+        chn = letter(c + 2 <= ncol ? c + 2 : ncol);
+        column_step<W>(V, M);
+        if (lane == 0) store_words<W>(out + c * W, V);
+#pragma unroll
+        for (int w = 0; w < W; ++w) M[w] = Mn[w];
+    }
+}
+
+// Strips whose segment of b is longer than kLeafSmemCols: warp 0 alone, the
+// forward vectors in the global scratch, then one lane walks back from the
+// sink: left while F keeps its value, else along the match diagonal if it
+// is tight, else up (which leaves each row at its leftmost vertex).
+template <int W>
+__device__ void leaf_walk_global(const LeafParams &p, int s, int64_t r0, int hs, int64_t i, int64_t j,
+                                 const uint32_t *fm, const uint8_t *sa, int lane) {
+    uint32_t *vb = p.vbuf + (i + s) * (int64_t)W;
     uint32_t V[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) V[w] = 0xFFFFFFFFu;
     if (lane < W) vb[lane] = 0xFFFFFFFFu;
-    if (kSmem && lane <= W) pp[lane] = (uint16_t)(32 * lane);
     for (int64_t c = i + 1; c <= j; ++c) {
-        const uint32_t *M = fm + bch(c) * W;
-        uint32_t u[W], sm[W];
+        const uint32_t *m = fm + p.b[c - 1] * W;
+        uint32_t M[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) u[w] = V[w] & M[w];
-        uint32_t carry = 0;
+        for (int w = 0; w < W; ++w) M[w] = m[w];
+        column_step<W>(V, M);
+        uint32_t mine = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint64_t t = (uint64_t)V[w] + (uint64_t)u[w] + carry;
-            sm[w] = (uint32_t)t;
-            carry = (uint32_t)(t >> 32);
-        }
-        uint32_t mine = 0;                       // word `lane` of V, picked without branches
-        int below = 0;                           // ones in the words below `lane`
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            V[w] = sm[w] | (V[w] & ~M[w]);
-            mine = lane == w ? V[w] : mine;
-            below += w < lane ? __popc(V[w]) : 0;
-        }
+        for (int w = 0; w < W; ++w) mine = lane == w ? V[w] : mine;
         if (lane < W) vb[(c - i) * W + lane] = mine;
-        if (kSmem && lane <= W) pp[(c - i) * (W + 1) + lane] = (uint16_t)below;
     }
     int ones = 0;
 #pragma unroll
@@ -146,22 +201,11 @@ __device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0
     const int Ltot = 32 * W - ones;              // padding bits stay 1
     __syncwarp();
     if (lane != 0) return;
-
-    // Backward walk (one lane).  F(r, c) = r minus the ones among the first
-    // r bits of V_c.
     auto F = [&](int64_t c, int r) -> int {
-        const uint32_t *v = vb + (c - i) * W;
-        if constexpr (kSmem) {
-            const int w = r >> 5, bits = r & 31;
-            int ones = pp[(c - i) * (W + 1) + w];
-            if (bits) ones += __popc(v[w] & ((1u << bits) - 1u));
-            return r - ones;
-        } else {
-            uint32_t vv[W];
+        uint32_t vv[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) vv[w] = v[w];
-            return f_at<W>(vv, r);
-        }
+        for (int w = 0; w < W; ++w) vv[w] = vb[(c - i) * W + w];
+        return r - prefix_ones<W>(vv, r);
     };
     int r = hs;
     int64_t c = j;
@@ -169,11 +213,11 @@ __device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0
     int fc = F(c, r);
     while (r > 0) {
         if (c > i) {
-            if (F(c - 1, r) == fc) {              // left along row r
+            if (F(c - 1, r) == fc) {
                 --c;
                 continue;
             }
-            if (sa[r - 1] == bch(c) && F(c - 1, r - 1) == fc - 1) {   // diagonal into row r
+            if (sa[r - 1] == p.b[c - 1] && F(c - 1, r - 1) == fc - 1) {
                 if (p.cross) p.cross[r0 + r] = (int32_t)c;
                 --pos;
                 if (pos >= 0) p.slots[(int64_t)s * p.h + pos] = sa[r - 1];
@@ -183,73 +227,186 @@ __device__ __forceinline__ void leaf_path(const LeafParams &p, int s, int64_t r0
                 continue;
             }
         }
-        if (p.cross) p.cross[r0 + r] = (int32_t)c;   // up: row r is entered at c
+        if (p.cross) p.cross[r0 + r] = (int32_t)c;
         --r;
         fc = F(c, r);
     }
-    // Row 0 of the strip is entered at its source i (the path may run along
-    // that row before stepping down, so the walk may stop right of i).
     if (s == 0 && p.cross) p.cross[0] = (int32_t)i;
     p.counts[s] = Ltot;
     if (pos != 0) set_error(p.err, ERR_BOUNDS);
 }
 
-// One warp per strip.  A forward bit-vector sweep from the strip's source i
-// stores V_c, c = i..j.  Then one lane walks back from the strip's sink
-// (h, j): left while F keeps its value (the heaviest path may run along the
-// row), else along the match diagonal if it is tight, else up.  Moving left
-// first keeps every row's segment as far left as it can go, so the row a
-// step leaves is left at its cross vertex v[r] = min{c : F(r,c)+B(r,c) =
-// DIST_strip(i, j)}: the leftmost heaviest path (Sec. II-C); a diagonal step
-// into row r marks letter a_r (Sec. II-E).
 template <int W>
-__global__ void __launch_bounds__(kLeafWarps * 32) leaf_kernel(LeafParams p) {
+__global__ void __launch_bounds__(kLeafThreads, 1) leaf_kernel(LeafParams p) {
     pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + warp * leaf_warp_bytes(W));   // [256][W] match masks
-    uint32_t *vs = fm + 256 * W;                                                  // [kLeafSmemCols][W]
-    uint16_t *pp = reinterpret_cast<uint16_t *>(vs + kLeafSmemCols * W);          // [kLeafSmemCols][W + 1]
-    uint8_t *sa = reinterpret_cast<uint8_t *>(pp + kLeafSmemCols * (W + 1));      // the strip's letters
-    uint8_t *sb = sa + 256;                                                       // b[i .. j - 1]
-    const int s = blockIdx.x * kLeafWarps + warp;
-    if (s >= p.S) return;
+    constexpr LeafSmem SL = leaf_smem_layout(W);
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + SL.fm);
+    uint32_t *fmr = reinterpret_cast<uint32_t *>(smem + SL.fmr);
+    uint32_t *vf = reinterpret_cast<uint32_t *>(smem + SL.vf);
+    uint32_t *vbk = reinterpret_cast<uint32_t *>(smem + SL.vb);
+    uint32_t *vr = reinterpret_cast<uint32_t *>(smem + SL.vr);
+    int32_t *vmin = reinterpret_cast<int32_t *>(smem + SL.vmin);
+    int32_t *wsum = reinterpret_cast<int32_t *>(smem + SL.wsum);
+    uint8_t *sa = smem + SL.sa;
+    uint8_t *sb = smem + SL.sb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = blockIdx.x;
     const int64_t r0 = (int64_t)s * p.h;
     const int hs = (int)min((int64_t)p.h, p.m - r0);
     const int64_t i = p.pathI[s], j = p.pathJ[s];
 
-    for (int t = lane; t < 256 * W; t += 32) fm[t] = 0u;
-    __syncwarp();
-    for (int r = lane; r < hs; r += 32) {
+    for (int t = tid; t < 256 * W; t += kLeafThreads) {
+        fm[t] = 0u;
+        fmr[t] = 0u;
+    }
+    for (int t = tid; t <= 256; t += kLeafThreads) vmin[t] = INT32_MAX;
+    __syncthreads();
+    for (int r = tid; r < hs; r += kLeafThreads) {
         const uint8_t ch = p.a[r0 + r];
         sa[r] = ch;
         atomicOr(&fm[ch * W + (r >> 5)], 1u << (r & 31));
+        const int rr = hs - 1 - r;               // row r of the reversed strip
+        atomicOr(&fmr[ch * W + (rr >> 5)], 1u << (rr & 31));
     }
-    __syncwarp();
-    if (i < 0 || j < i || j > p.n) {
-        if (lane == 0) { set_error(p.err, ERR_BOUNDS); p.counts[s] = 0; }
+    const bool valid = !(i < 0 || j < i || j > p.n);
+    const int64_t ncol64 = valid ? j - i : 0;
+    if (valid && ncol64 <= kLeafSmemCols)
+        for (int64_t t = tid; t < ncol64; t += kLeafThreads) sb[t] = p.b[i + t];
+    __syncthreads();
+    if (!valid) {
+        if (tid == 0) {
+            set_error(p.err, ERR_BOUNDS);
+            p.counts[s] = 0;
+        }
         return;
     }
-    const int64_t ncol = j - i + 1;
-    if (ncol <= kLeafSmemCols) {
-        // The letters the serial sweep and walk compare, and the column
-        // vectors, live in shared memory; a global access per step would
-        // dominate the walk.
-        for (int64_t t = lane; t < ncol - 1; t += 32) sb[t] = p.b[i + t];
-        __syncwarp();
-        leaf_path<W, true>(p, s, r0, hs, i, j, fm, vs, pp, sa, sb, lane);
-    } else {
-        leaf_path<W, false>(p, s, r0, hs, i, j, fm, p.vbuf + (i + s) * (int64_t)W, nullptr, sa, nullptr, lane);
+    if (ncol64 > kLeafSmemCols) {
+        if (warp == 0) leaf_walk_global<W>(p, s, r0, hs, i, j, fm, sa, lane);
+        return;
+    }
+    const int ncol = (int)ncol64;
+    if (warp == 0) leaf_sweep<W>(fm, sb, ncol, false, vf, lane);
+    else if (warp == 1) leaf_sweep<W>(fmr, sb, ncol, true, vbk, lane);
+    __syncthreads();
+
+    // Backward vectors in forward row order: bit q of vr[c'] is bit
+    // hs - 1 - q of vbk[c'] (reverse all 32 W bits, then drop the 32 W - hs
+    // padding rows that land at the bottom).  A thread per column.
+    {
+        const int sft = 32 * W - hs, q0 = sft >> 5, sb5 = sft & 31;
+        for (int c = tid; c <= ncol; c += kLeafThreads) {
+            // Word k of the reversed vector is brev(vbk word W - 1 - k); word
+            // w of the result joins reversed words w + q0 and w + q0 + 1.
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int klo = W - 1 - (w + q0), khi = klo - 1;
+                const uint32_t lo = klo >= 0 ? __brev(vbk[c * W + klo]) : 0u;
+                const uint32_t hi = khi >= 0 ? __brev(vbk[c * W + khi]) : 0u;
+                vr[c * W + w] = sb5 ? ((lo >> sb5) | (hi << (32 - sb5))) : lo;
+            }
+        }
+    }
+    __syncthreads();
+
+    // L = F(hs, j).  Vertex (r, c) lies on a heaviest path iff F + B = L,
+    // i.e. ones(vf[c - i], bits < r) + ones(vr[j - c], bits r .. hs-1)
+    // = hs - L.  A lane per column (32 consecutive columns per warp and
+    // group) runs down the rows, the count moving by (forward bit - backward
+    // bit) of row r - 1, and collects its hits as bit masks of 32 rows; a
+    // warp bit-matrix transpose then gives lane t, for row 32 w + t + 1, the
+    // mask of the group's columns with a hit, whose lowest bit is the
+    // group's smallest such column.
+    uint32_t last[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) last[w] = vf[ncol * W + w];
+    const int L = hs - prefix_ones<W>(last, hs);
+    const int target = hs - L;
+    const int nw = kLeafThreads / 32;
+    for (int grp = warp; grp * 32 <= ncol; grp += nw) {
+        const int c = grp * 32 + lane;
+        const bool live = c <= ncol;
+        const uint32_t *fc = vf + c * W, *gc = vr + (ncol - c) * W;
+        int d = INT32_MIN / 2;                   // dead lanes never hit
+        if (live) {
+            d = 0;                               // r = 0: all of B's ones
+            for (int w = 0; w < W; ++w) {
+                const int k = min(max(hs - 32 * w, 0), 32);
+                d += __popc(gc[w] & (k == 32 ? 0xFFFFFFFFu : ((1u << k) - 1u)));
+            }
+        }
+        for (int w = 0; w < W && 32 * w < hs; ++w) {
+            uint32_t fw = live ? fc[w] : 0u, gw = live ? gc[w] : 0u, hits = 0u;
+            // Partly unrolled: fully unrolled rows of every word would not
+            // fit the instruction cache.
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) {
+                d += (int)(fw & 1u) - (int)(gw & 1u);
+                fw >>= 1;
+                gw >>= 1;
+                hits |= (d == target ? 1u : 0u) << t;
+            }
+            // Rows past hs within the word carry padding bits: drop them.
+            const int valid = hs - 32 * w;
+            if (valid < 32) hits &= (1u << valid) - 1u;
+            // Transpose: afterwards lane t holds bit l = hit of lane l's
+            // column in row 32 w + t + 1.
+#pragma unroll
+            for (int sh = 16; sh >= 1; sh >>= 1) {
+                const uint32_t m = sh == 16 ? 0x0000FFFFu : sh == 8 ? 0x00FF00FFu : sh == 4 ? 0x0F0F0F0Fu
+                                                            : sh == 2 ? 0x33333333u : 0x55555555u;
+                const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, hits, sh);
+                hits = (lane & sh) ? ((hits & ~m) | ((y & ~m) >> sh)) : ((hits & m) | ((y & m) << sh));
+            }
+            if (hits) atomicMin(&vmin[32 * w + lane + 1], grp * 32 + __ffs(hits) - 1);
+        }
+    }
+    __syncthreads();
+
+    // Marks, their ranks (block scan), the cross vertices and the letters.
+    const int r = tid + 1;                       // one row per thread (hs <= 256)
+    bool mark = false, bad = false;
+    int32_t v = 0;
+    if (r <= hs) {
+        const int32_t cr = vmin[r], cp = r == 1 ? 0 : vmin[r - 1];
+        bad = cr == INT32_MAX || cp == INT32_MAX;
+        if (!bad) {
+            v = (int32_t)i + cr;
+            mark = cr > cp && sa[r - 1] == sb[cr - 1];
+        }
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, mark);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) {
+            set_error(p.err, ERR_BOUNDS);
+            p.counts[s] = 0;
+        }
+        return;
+    }
+    int before = __popc(bal & ((1u << lane) - 1u)), total = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) before += wsum[w];
+        total += wsum[w];
+    }
+    if (r <= hs) {
+        if (p.cross) p.cross[r0 + r] = v;
+        if (mark) p.slots[(int64_t)s * p.h + before] = sa[r - 1];
+    }
+    if (tid == 0) {
+        if (s == 0 && p.cross) p.cross[0] = (int32_t)i;
+        p.counts[s] = total;
+        if (total != L) set_error(p.err, ERR_BOUNDS);
     }
 }
 
 template <int W>
 static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
-    const size_t smem = (size_t)kLeafWarps * leaf_warp_bytes(W);
+    constexpr size_t smem = leaf_smem_layout(W).total;
     auto kern = leaf_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kern, dim3((unsigned)ceil_div(p.S, kLeafWarps)), dim3(kLeafWarps * 32), smem, st, p);
+    return launch_pdl(kern, dim3((unsigned)p.S), dim3(kLeafThreads), smem, st, p);
 }
 
 cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st) {
