@@ -38,7 +38,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["iid", "correlated"], default="iid")
-    ap.add_argument("--strip-height", type=int, default=0)
+    ap.add_argument("--strip-height", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA-graph replay")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -58,10 +59,11 @@ def workload(variant, rank):
     return a, b
 
 
-def config_dict(variant, m, n, h):
+def config_dict(variant, m, n, h, merge_kernel, graphs):
     return {"workload": "single pair m=n=4096, ACGT %s: int32 DIST of the whole grid + LCS length + "
                         "leftmost-argmax LCS" % variant,
             "m": m, "n": n, "variant": variant, "dist_dtype": "int32", "strip_height": h,
+            "merge_kernel": {1: "exact", 2: "dpx"}.get(merge_kernel, "auto"), "cuda_graphs": graphs,
             "l2": "flushed between steps (256 MiB write outside the timed events)"}
 
 
@@ -328,6 +330,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    tuned = {"merge_kernel": 0}
+    if args.strip_height == 0:
+        tuned = B.lcs_autotune(ctx, ad, bd, dist=dist_out, out_lcs=lcs_out, stream=stream)
+    graphs = not args.no_graphs
+    B.lcs_set_graphs(ctx, graphs)
+
     def step():
         B.lcs_solve(ctx, ad, bd, dist=dist_out, out_lcs=lcs_out, out_len=len_out, stream=stream)
 
@@ -397,7 +405,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": config_dict(args.variant, m, n, stats["strip_height"]),
+            "config": config_dict(args.variant, m, n, stats["strip_height"], tuned["merge_kernel"], graphs),
             "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
             "roofline": roofline(profile, peaks, peaks_src, int_peak),
             "clocks": clock_info,

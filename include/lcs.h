@@ -136,6 +136,28 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
 enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2 };
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
 
+/* CUDA-graph replay of lcs_solve (1) or plain launches (0, the default).
+ * With graphs on, the first lcs_solve with a given set of arguments runs as
+ * usual and is then captured (on a private stream) into a graph; later
+ * calls with the same arguments, strip height, merge kernel and device plan
+ * replay it with one launch on the caller's stream.  One graph is kept: a
+ * call with other arguments re-captures.  Calls with profiling on, and
+ * empty strings, always launch directly.  Errors: EINVAL, ECUDA. */
+lcs_status lcs_set_graphs(lcs_ctx *ctx, int32_t enable);
+
+/* Autotuner: times the caller's solve (the same outputs: dist may be NULL,
+ * out_lcs may be NULL) at strip heights 64, 128 and 256 and, where the
+ * plan allows both, with the DPX and the exact merge kernel, and keeps the
+ * fastest for the size bucket (floor(log2 m), floor(log2 n), dtype).  Later
+ * solves with the automatic strip height (lcs_set_strip_height(ctx, 0)) and
+ * merge kernel in that bucket use it.  The outputs hold the last timed
+ * solve's results, which do not depend on the choice.  Synchronous.
+ * h_out, merge_out, ms_out (nullable) receive the choice and its time.
+ * Errors: EINVAL, ENOMEM (no candidate fits the budget), ECUDA, ETIMEOUT. */
+lcs_status lcs_autotune(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, lcs_dtype dtype,
+                        void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap, void *stream,
+                        int32_t *h_out, int32_t *merge_out, float *ms_out);
+
 /* Counters of the last call (see lcs_stats).  Errors: EINVAL. */
 lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out);
 

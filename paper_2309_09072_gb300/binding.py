@@ -108,6 +108,9 @@ def load(path: str = LIB_PATH):
             "lcs_last_error": ([vp], ctypes.c_char_p),
             "lcs_set_strip_height": ([vp, i32], st),
             "lcs_set_merge_kernel": ([vp, i32], st),
+            "lcs_set_graphs": ([vp, i32], st),
+            "lcs_autotune": ([vp, vp, i64, vp, i64, i32, vp, i64, vp, i64, vp, ctypes.POINTER(i32),
+                              ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
             "lcs_sync": ([vp, vp], st),
             "lcs_set_profiling": ([vp, i32], st),
@@ -210,6 +213,23 @@ LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX = 0, 1, 2
 
 def lcs_set_merge_kernel(ctx, kind: int) -> None:
     _check(ctx, load().lcs_set_merge_kernel(ctx, int(kind)))
+
+
+def lcs_set_graphs(ctx, enable: bool) -> None:
+    _check(ctx, load().lcs_set_graphs(ctx, 1 if enable else 0))
+
+
+def lcs_autotune(ctx, a, b, dist=None, out_lcs=None, stream=None) -> dict:
+    """Time the candidate strip heights / merge kernels on this call's shape
+    and outputs; returns the choice kept for the size bucket."""
+    dtype = _dtype_of(dist) if dist is not None else LCS_I32
+    ld = _ld(dist) if dist is not None else 0
+    cap = int(out_lcs.numel()) if out_lcs is not None else 0
+    h, mk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(ctx, load().lcs_autotune(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), dtype, _ptr(dist), ld,
+                                    _ptr(out_lcs), cap, _stream(stream), ctypes.byref(h), ctypes.byref(mk),
+                                    ctypes.byref(ms)))
+    return {"strip_height": h.value, "merge_kernel": mk.value, "ms": ms.value}
 
 
 def lcs_get_stats(ctx) -> dict:

@@ -167,6 +167,17 @@ struct lcs_ctx {
     size_t batch_bytes = 0;
     std::vector<BatchLane> free_lanes;    // streams/events of released batches
     cudaMemPool_t mempool = nullptr;      // batches' device memory (stream ordered, no device sync)
+    // CUDA-graph replay of lcs_solve (lcs_set_graphs)
+    bool graphs = false;
+    cudaStream_t cap_stream = nullptr;    // private stream the solve is captured on
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int64_t> gkey;            // the arguments and plan state the graph was captured for
+    int32_t glaunches = 0;
+    // autotuner (lcs_autotune): (m bucket, n bucket, root dtype, wants dist) -> (h, merge kernel)
+    std::map<std::vector<int64_t>, std::pair<int32_t, int32_t>> tuned;
+    int32_t tuned_merge = -1;             // merge kernel chosen with the current automatic h, -1: none
+    int64_t tune_gen = 0;                 // bumped by every lcs_autotune
+    int64_t plan_gen = 0;                 // bumped whenever the device copy of the plan is rewritten
 };
 
 namespace {
@@ -437,13 +448,28 @@ int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
 }
 
 // Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
+// Size bucket of the autotuner: floor(log2) of each length and the root
+// dtype (the dense output, when asked for, changes the root merge's work).
+std::vector<int64_t> tune_key(int64_t m, int64_t n, int root_dt) {
+    auto lg = [](int64_t x) { int64_t b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
+    return {lg(m), lg(n), (int64_t)root_dt};
+}
+
 lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
     Plan &P = ctx->plan;
     int h = ctx->strip_h;
+    ctx->tuned_merge = -1;
     if (h <= 0) {
-        // Reuse the current plan's choice for the same shape.
-        h = (P.m == m && P.n == n && P.root_dt == root_dt && ctx->auto_h) ? P.h
-                                                                           : choose_strip_height(ctx, m, n, root_dt);
+        // A tuned choice for this size bucket, else the current plan's
+        // choice for the same shape, else the rule.
+        auto it = ctx->tuned.find(tune_key(m, n, root_dt));
+        if (it != ctx->tuned.end()) {
+            h = it->second.first;
+            ctx->tuned_merge = it->second.second;
+        } else {
+            h = (P.m == m && P.n == n && P.root_dt == root_dt && ctx->auto_h) ? P.h
+                                                                               : choose_strip_height(ctx, m, n, root_dt);
+        }
         ctx->auto_h = true;
     } else {
         ctx->auto_h = false;
@@ -483,6 +509,7 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
                                    cudaMemcpyHostToDevice));
         }
         ctx->plan_uploaded = true;
+        ++ctx->plan_gen;
     }
     return LCS_OK;
 }
@@ -606,7 +633,8 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 mp.sigma = (int32_t)sg; mp.full = 0;
                 LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
             }
-            const int mk = ctx->merge_kernel;
+            const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
+                           : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
             if (P.dpx && mk != LCS_MERGE_EXACT) {
                 LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
                             0.0, launch_tile_dpx(mp, g.out_dt, st));
@@ -713,6 +741,8 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
     for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return LCS_OK;
 }
@@ -742,6 +772,81 @@ lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
     if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
     ctx->merge_kernel = kind;
     return LCS_OK;
+}
+
+lcs_status lcs_set_graphs(lcs_ctx *ctx, int32_t enable) {
+    if (!ctx) return LCS_EINVAL;
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs && ctx->gexec) {
+        LCS_CK(ctx, cudaSetDevice(ctx->device));
+        LCS_CK(ctx, cudaDeviceSynchronize());
+        LCS_CK(ctx, cudaGraphExecDestroy(ctx->gexec));
+        ctx->gexec = nullptr;
+        ctx->gkey.clear();
+    }
+    return LCS_OK;
+}
+
+lcs_status lcs_autotune(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, lcs_dtype dtype,
+                        void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap, void *stream,
+                        int32_t *h_out, int32_t *merge_out, float *ms_out) {
+    if (!ctx) return LCS_EINVAL;
+    if (m <= 0 || n <= 0) return fail(ctx, LCS_EINVAL, "autotune needs m, n > 0");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int root_dt = api_dt(dtype);
+    const std::vector<int64_t> key = tune_key(m, n, root_dt);
+    const int32_t keep_h = ctx->strip_h, keep_mk = ctx->merge_kernel;
+    const bool keep_prof = ctx->profiling, keep_graphs = ctx->graphs;
+    ctx->profiling = false;
+    ctx->graphs = false;
+    ctx->tuned.erase(key);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LCS_CK(ctx, cudaEventCreate(&e0));
+    LCS_CK(ctx, cudaEventCreate(&e1));
+    float best_ms = -1.0f;
+    int32_t best_h = 0, best_mk = LCS_MERGE_AUTO;
+    lcs_status s = LCS_OK;
+    const int32_t hs[3] = {64, 128, 256};
+    const int32_t mks[2] = {LCS_MERGE_DPX, LCS_MERGE_EXACT};
+    for (int32_t h : hs) {
+        if (h > m && h != hs[0]) continue;          // taller than the pair: same plan as a shorter h
+        for (int32_t mk : mks) {
+            ctx->strip_h = std::min<int64_t>(h, m);
+            ctx->merge_kernel = mk;
+            s = solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, nullptr, nullptr, true, st);
+            if (s == LCS_ENOMEM) { s = LCS_OK; continue; }      // does not fit the budget: not a candidate
+            if (s != LCS_OK) break;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && s == LCS_OK; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) { s = LCS_ECUDA; break; }
+                s = solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, nullptr, nullptr, true, st);
+                if (s != LCS_OK) break;
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { s = LCS_ECUDA; break; }
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = std::min(ms, t);
+            }
+            if (s != LCS_OK) break;
+            if (best_ms < 0.0f || ms < best_ms) { best_ms = ms; best_h = ctx->strip_h; best_mk = mk; }
+            if (!ctx->plan.dpx) break;               // the plan has no DPX merge: one kernel to time
+        }
+        if (s != LCS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->strip_h = keep_h;
+    ctx->merge_kernel = keep_mk;
+    ctx->profiling = keep_prof;
+    ctx->graphs = keep_graphs;
+    if (s != LCS_OK) return s;
+    if (best_ms < 0.0f) return fail(ctx, LCS_ENOMEM, "no strip height fits the budget");
+    ctx->tuned[key] = {best_h, best_mk};
+    ++ctx->tune_gen;
+    if (h_out) *h_out = best_h;
+    if (merge_out) *merge_out = best_mk;
+    if (ms_out) *ms_out = best_ms;
+    return read_back(ctx, st, nullptr);
 }
 
 lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out) {
@@ -874,8 +979,61 @@ lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b
                      int64_t *out_len_device, void *stream) {
     if (!ctx) return LCS_EINVAL;
     LCS_CK(ctx, cudaSetDevice(ctx->device));
-    return solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, cross, out_len_device, false,
-                        (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->graphs || ctx->profiling || m == 0 || n == 0)
+        return solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, cross, out_len_device, false, st);
+    // Graph replay: the launch sequence depends only on the arguments and on
+    // the plan state (strip height, merge kernel, workspace), so a solve with
+    // the same key replays the captured graph.
+    std::vector<int64_t> key = {(int64_t)(uintptr_t)a, m, (int64_t)(uintptr_t)b, n, (int64_t)dtype,
+                                (int64_t)(uintptr_t)dist, ld, (int64_t)(uintptr_t)out_lcs, cap,
+                                (int64_t)(uintptr_t)cross, (int64_t)(uintptr_t)out_len_device,
+                                ctx->strip_h, ctx->merge_kernel, ctx->tune_gen};
+    // The captured kernels read the plan's descriptors from the workspace:
+    // a graph stays valid only while that copy of the plan is the one it
+    // was captured with.
+    auto with_plan = [&](std::vector<int64_t> k) {
+        k.push_back((int64_t)(uintptr_t)ctx->ws);
+        k.push_back(ctx->plan_gen);
+        return k;
+    };
+    if (ctx->gexec && ctx->gkey == with_plan(key)) {
+        LCS_CK(ctx, cudaGraphLaunch(ctx->gexec, st));
+        ctx->launches = ctx->glaunches;
+        ctx->stats.kernel_launches = ctx->glaunches;
+        return LCS_OK;
+    }
+    // Miss: run eagerly (this prepares the plan and workspace, so the
+    // capture below makes no allocation or synchronous copy), then capture
+    // the same solve on the private stream for the next calls.
+    lcs_status s = solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, cross, out_len_device, false, st);
+    if (s != LCS_OK) return s;
+    if (!ctx->cap_stream) LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (ctx->gexec) {
+        LCS_CK(ctx, cudaGraphExecDestroy(ctx->gexec));
+        ctx->gexec = nullptr;
+    }
+    const lcs_stats keep = ctx->stats;
+    const std::vector<int64_t> full = with_plan(key);
+    LCS_CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    s = solve_device(ctx, a, m, b, n, dtype, dist, ld, out_lcs, cap, cross, out_len_device, false, ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (s != LCS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        ctx->gexec = nullptr;
+        return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+    }
+    ctx->gkey = full;
+    ctx->glaunches = ctx->launches;
+    ctx->stats = keep;
+    return LCS_OK;
 }
 
 lcs_status lcs_dist(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, lcs_dtype dtype,
