@@ -83,7 +83,10 @@ struct Plan {
     std::vector<TbMerge> h_tb;
 };
 
-constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int64) at 8
+constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int64) at 8,
+                                       // DPX tile counters (one per tree level) at 64
+constexpr size_t kSchedOffset = 64;
+constexpr int kSchedSlots = 32;
 
 // A submitted batch: its stream, completion events and one device block
 // holding descriptors, lengths, strings, column vectors and an error word.
@@ -577,6 +580,10 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     int32_t *counts = reinterpret_cast<int32_t *>(base + P.off_counts);
     uint8_t *slots = reinterpret_cast<uint8_t *>(base + P.off_slots);
 
+    // DPX merge tile counters, one per tree level (zero at each launch).
+    unsigned int *sched = reinterpret_cast<unsigned int *>(base + kSchedOffset);
+    if (P.dpx && P.S > 1) LCS_CK(ctx, cudaMemsetAsync(sched, 0, kSchedSlots * sizeof(unsigned int), st));
+
     // 1. strips
     if (P.S == 1) {
         if (dist) {
@@ -618,6 +625,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         }
         // 2. merges, level by level
         const int64_t sigma0 = coarse_sigma0(P.P);
+        int dpx_launch = 0;
         for (const Group &g : P.groups) {
             if (g.root && !dist) continue;
             MergeParams mp{};
@@ -636,6 +644,9 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
                            : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
             if (P.dpx && mk != LCS_MERGE_EXACT) {
+                // A zeroed tile counter per launch (zeroed above, once per solve).
+                mp.sched = dpx_launch < kSchedSlots ? sched + dpx_launch : nullptr;
+                ++dpx_launch;
                 LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
                             0.0, launch_tile_dpx(mp, g.out_dt, st));
             } else {

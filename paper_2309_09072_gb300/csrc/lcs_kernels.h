@@ -57,7 +57,8 @@ struct MergeParams {
     int32_t spill;         // 0: tiles whose band fits `cap`; 1: the others
     int32_t cap_main;      // the main launch's cap (spill launches only)
     int32_t const_tiles;   // 1: write tiles whose corner values agree as constants
-    int32_t pad;
+    int32_t grab;          // DPX launch: tiles taken from `sched` at a time (set by the launcher)
+    unsigned int *sched;   // DPX launch: tile counter (zero at launch) for dynamic scheduling, or null
 };
 
 // K-tiles per band for the main tile launch and the spill launch.

@@ -676,7 +676,7 @@ cudaError_t launch_tile(const MergeParams &p, int in_dtype, int out_dtype, cudaS
 // product has read the shared-memory band, so they land while the current
 // tile is stored and the constant tiles in between are written.
 constexpr int kDpxThreads = 128;
-constexpr int kDpxCap = 3;
+constexpr int kDpxCap = 2;
 constexpr int16_t kNegInf16 = -16384;
 
 struct DpxSmem {
@@ -717,6 +717,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
     __shared__ int s_ok;
     __shared__ DpxMeta s_meta[32];
+    __shared__ int64_t s_grab;
 
     const int64_t NT = p.NT, P = p.P;
     const int n = (int)p.n;
@@ -745,13 +746,29 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
         }
     };
 
-    for (int64_t b0 = blockIdx.x; b0 < total; b0 += 32 * G) {
+    // Batches of tiles: with a counter, p.grab (1..32) consecutive tiles
+    // taken from it (tile costs differ by orders of magnitude -- constant
+    // tiles read nothing, wide bands stream several chunks -- so a static
+    // split leaves SMs idle at the end); without one, 32 tiles strided by the
+    // grid.
+    const int64_t bstride = p.sched ? 1 : G;
+    const int bcount = p.sched ? p.grab : 32;
+    for (int64_t it = 0;; ++it) {
         __syncthreads();                       // the previous batch's metadata is consumed
+        int64_t b0;
+        if (p.sched) {
+            if (threadIdx.x == 0) s_grab = (int64_t)atomicAdd(p.sched, (unsigned)bcount);
+            __syncthreads();
+            b0 = s_grab;
+        } else {
+            b0 = blockIdx.x + it * 32 * G;
+        }
+        if (b0 >= total) break;
         if (threadIdx.x < 32) {
-            // Lane l classifies tile b0 + l * G.
-            const int64_t g = b0 + lane * G;
+            // Lane l classifies tile b0 + l * bstride.
+            const int64_t g = b0 + lane * bstride;
             DpxMeta m{};
-            if (g < total) {
+            if (lane < bcount && g < total) {
                 m.valid = 1;
                 m.job = (int)(g / tiles);
                 const int64_t tix = g - m.job * tiles;
@@ -960,7 +977,13 @@ static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDpxThreads, smem)) != cudaSuccess) return e;
     const int64_t work = p.njobs * num_tiles_tri(p.NT);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
-    return launch_pdl(kern, dim3((unsigned)grid), dim3(kDpxThreads), smem, st, p);
+    // Tiles per grab: larger grabs amortise the classification's load
+    // latency, smaller ones shorten the tail; measured best at 2 with ~20
+    // tiles per CTA (4096) and 4-8 with ~1000 (16384).
+    MergeParams q = p;
+    const int64_t per_cta = work / grid;
+    q.grab = per_cta >= 96 ? 8 : per_cta >= 48 ? 4 : per_cta >= 16 ? 2 : 1;
+    return launch_pdl(kern, dim3((unsigned)grid), dim3(kDpxThreads), smem, st, q);
 }
 
 cudaError_t launch_tile_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
