@@ -252,6 +252,35 @@ lcs_status lcs_length(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *
 lcs_status lcs_traceback(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                          uint8_t *out_lcs, int64_t cap, int64_t *out_len_host, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Breakout (D-form) matrices: the paper's compact form of a strip's DIST
+ * (Sec. II-B-1).  D(i, w) = min{ j >= i : DIST(i, j) >= w } is the leftmost
+ * bottom vertex reached from top vertex i with weight w; D(i, 0) = i; an
+ * unreachable weight holds INT32_MAX (LCS_I32) or INT16_MAX (LCS_I16).  A
+ * strip of h rows takes (n+1) x (h+1) entries, row-major with leading
+ * dimension ld (elements), row i = D(i, 0..h).  Device pointers, owned by
+ * the caller; asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+
+/* D-forms of the S = ceil(m / h) strips of h (1..256) rows of a (m
+ * letters; the last strip may be shorter, its unreachable weights hold the
+ * infinity) against b (n columns), in one launch.  Strip s is stored at
+ * dform + s * (n+1) * ldf elements.  ldf >= h + 1; S <= 65535.  LCS_I16
+ * needs n < 32767.  Errors: EINVAL, ECUDA. */
+lcs_status lcs_strip_dform(lcs_ctx *ctx, const uint8_t *a, int64_t m, int32_t h, const uint8_t *b, int64_t n,
+                           lcs_dtype dtype, void *dform, int64_t ldf, void *stream);
+
+/* The combination of Sec. II-B-3 of an upper (hu rows) and a lower (hl
+ * rows) strip over the same b:
+ *     out(i, w) = min_{0 <= k <= w} dl(du(i, k), w - k),   w = 0 .. hu + hl,
+ * terms with du(i, k) unreachable or w - k > hl left out.  Computed by
+ * monotone column minima per top vertex (Algorithm 1 cut to two levels:
+ * the exact minimum of every 32nd column bounds the rows of the columns in
+ * between).  hu + hl <= 16384; ldu >= hu + 1, ldl >= hl + 1,
+ * ldo >= hu + hl + 1.  Errors: EINVAL, ECUDA. */
+lcs_status lcs_dform_merge(lcs_ctx *ctx, const void *du, int32_t hu, int64_t ldu, const void *dl, int32_t hl,
+                           int64_t ldl, int64_t n, lcs_dtype dtype, void *out, int64_t ldo, void *stream);
+
 /* The leftmost heaviest path itself, as the list of its grid vertices
  * (Sec. II-D: each row's horizontal run between consecutive cross vertices,
  * the runs placed in row order by a prefix sum).  Vertex (r, c) is the

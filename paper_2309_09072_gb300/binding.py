@@ -124,6 +124,8 @@ def load(path: str = LIB_PATH):
             "lcs_length": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_traceback": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_path": ([vp, vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
+            "lcs_strip_dform": ([vp, vp, i64, i32, vp, i64, i32, vp, i64, vp], st),
+            "lcs_dform_merge": ([vp, vp, i32, i64, vp, i32, i64, i64, i32, vp, i64, vp], st),
             "lcs_solve": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, vp, vp, vp], st),
             "lcs_solve_host": ([vp, vp, i64, vp, i64, st, vp, i64, vp, i64, ctypes.POINTER(i64), vp], st),
             "lcs_batch_submit": ([vp, ctypes.POINTER(lcs_pair), i64, ctypes.POINTER(ctypes.c_uint64)], st),
@@ -304,6 +306,26 @@ def lcs_traceback(ctx, a, b, out_lcs, stream=None) -> int:
     _check(ctx, load().lcs_traceback(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(out_lcs),
                                      int(out_lcs.numel()), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def lcs_strip_dform(ctx, a, b, dform, h=None, stream=None) -> None:
+    """Breakout matrices of a's strips of h rows (default: one strip of all of
+    a) into ``dform``: shape (S, n+1, ldf) or, for one strip, (n+1, ldf);
+    int32 or int16."""
+    m = int(a.numel())
+    h = m if h is None else int(h)
+    d2 = dform if dform.dim() == 2 else dform[0]
+    if dform.dim() == 3 and dform.stride(0) != (int(b.numel()) + 1) * d2.stride(0):
+        raise ValueError("strips of dform must be contiguous (n+1) x ldf blocks")
+    _check(ctx, load().lcs_strip_dform(ctx, _ptr(a), m, h, _ptr(b), int(b.numel()), _dtype_of(d2), _ptr(dform),
+                                       _ld(d2), _stream(stream)))
+
+
+def lcs_dform_merge(ctx, du, hu, dl, hl, out, stream=None) -> None:
+    """Combination of two breakout matrices (rows = top vertices) into ``out``."""
+    n = int(du.shape[0]) - 1
+    _check(ctx, load().lcs_dform_merge(ctx, _ptr(du), int(hu), _ld(du), _ptr(dl), int(hl), _ld(dl), n,
+                                       _dtype_of(out), _ptr(out), _ld(out), _stream(stream)))
 
 
 def lcs_path(ctx, a, b, path, stream=None) -> int:

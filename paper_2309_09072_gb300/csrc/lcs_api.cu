@@ -934,6 +934,47 @@ lcs_status lcs_strip_dist(lcs_ctx *ctx, const uint8_t *a_strip, int32_t h, const
     return LCS_OK;
 }
 
+lcs_status lcs_strip_dform(lcs_ctx *ctx, const uint8_t *a, int64_t m, int32_t h, const uint8_t *b, int64_t n,
+                           lcs_dtype dtype, void *dform, int64_t ldf, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    ctx->launches = 0;
+    if (h < 1 || h > 256) return fail(ctx, LCS_EINVAL, "h must be 1..256");
+    if (m < 1 || ceil_div(m, h) > 65535) return fail(ctx, LCS_EINVAL, "m must be 1 .. 65535 h");
+    if (n < 0 || n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "n out of range");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    if (dtype == LCS_I16 && n >= INT16_MAX) return fail(ctx, LCS_EINVAL, "LCS_I16 needs n < 32767");
+    if (!a || (n > 0 && !b) || !dform) return fail(ctx, LCS_EINVAL, "a, b or dform is NULL");
+    if (ldf < h + 1) return fail(ctx, LCS_EINVAL, "ldf < h+1");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    DformStripParams dp{};
+    dp.a = a; dp.m = m; dp.h = h; dp.b = b; dp.n = n; dp.out = dform; dp.ld = ldf;
+    LCS_LAUNCHK(ctx, st, K_STRIP, (double)ceil_div(m, h) * (n + 1) * (h + 1) * dt_size(api_dt(dtype)), 0.0,
+                launch_dform_strip(dp, api_dt(dtype), words_for(h), st));
+    ctx->stats.kernel_launches = ctx->launches;
+    return LCS_OK;
+}
+
+lcs_status lcs_dform_merge(lcs_ctx *ctx, const void *du, int32_t hu, int64_t ldu, const void *dl, int32_t hl,
+                           int64_t ldl, int64_t n, lcs_dtype dtype, void *out, int64_t ldo, void *stream) {
+    if (!ctx) return LCS_EINVAL;
+    ctx->launches = 0;
+    if (hu < 0 || hl < 0 || hu + hl > 16384) return fail(ctx, LCS_EINVAL, "hu, hl must be >= 0 with hu + hl <= 16384");
+    if (n < 0 || n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "n out of range");
+    if (dtype != LCS_I32 && dtype != LCS_I16) return fail(ctx, LCS_EINVAL, "dtype");
+    if (dtype == LCS_I16 && n >= INT16_MAX) return fail(ctx, LCS_EINVAL, "LCS_I16 needs n < 32767");
+    if (!du || !dl || !out) return fail(ctx, LCS_EINVAL, "du, dl or out is NULL");
+    if (ldu < hu + 1 || ldl < hl + 1 || ldo < hu + hl + 1) return fail(ctx, LCS_EINVAL, "leading dimension too small");
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    DformMergeParams mp{};
+    mp.du = du; mp.dl = dl; mp.ldu = ldu; mp.ldl = ldl; mp.hu = hu; mp.hl = hl; mp.n = n; mp.out = out; mp.ldo = ldo;
+    LCS_LAUNCHK(ctx, st, K_TILE, (double)(n + 1) * (2 * hu + hl + 2) * dt_size(api_dt(dtype)), 0.0,
+                launch_dform_merge(mp, api_dt(dtype), st));
+    ctx->stats.kernel_launches = ctx->launches;
+    return LCS_OK;
+}
+
 lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64_t n, lcs_dtype dtype,
                      int64_t ld, void *dist_out, int32_t *argmax_out, void *stream) {
     if (!ctx) return LCS_EINVAL;

@@ -184,6 +184,27 @@ struct PathParams {
 };
 cudaError_t launch_path(const PathParams &p, cudaStream_t st);
 
+// Breakout (D-form) matrices (dform.cu).
+struct DformStripParams {
+    const uint8_t *a;      // m letters: strips of h rows (the last one may be shorter)
+    int64_t m;
+    int32_t h, pad;
+    const uint8_t *b;
+    int64_t n;
+    void *out;             // strip s at out + s * (n+1) * ld: (n+1) x ld, row i = D(i, 0..h)
+    int64_t ld;
+};
+cudaError_t launch_dform_strip(const DformStripParams &p, int dtype, int words, cudaStream_t st);
+struct DformMergeParams {
+    const void *du, *dl;   // (n+1) x (hu+1), (n+1) x (hl+1)
+    int64_t ldu, ldl;
+    int32_t hu, hl;
+    int64_t n;
+    void *out;             // (n+1) x (hu+hl+1)
+    int64_t ldo;
+};
+cudaError_t launch_dform_merge(const DformMergeParams &p, int dtype, cudaStream_t st);
+
 // Copy the internal length word to the caller's word (device to device).
 cudaError_t launch_copy_len(const int64_t *src, int64_t *dst, cudaStream_t st);
 

@@ -414,6 +414,34 @@ def test_dform_combine_equals_dist_merge(seed):
     assert np.array_equal(oracle.dform_combine(DU, DL), oracle.dform(D, m))
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_dform_combine_argmin_monotone(seed):
+    """Sec. II-B-1: for each top vertex the terms D_L(D_U(i, k), w - k) form a
+    monotone matrix -- the leftmost minimising k never decreases as w grows
+    -- which is what Algorithm 1's column-minima recursion (and the GPU's
+    two-level version of it) relies on.  Checked by brute force over every
+    column of random strips."""
+    rng = np.random.default_rng(900 + seed)
+    for _ in range(6):
+        hu, hl, n = int(rng.integers(1, 24)), int(rng.integers(1, 24)), int(rng.integers(0, 60))
+        alph = np.frombuffer([b"AC", b"ACGT", bytes(range(20))][int(rng.integers(0, 3))], np.uint8)
+        a1, a2, b = inputs.uniform(rng, hu, alph), inputs.uniform(rng, hl, alph), inputs.uniform(rng, n, alph)
+        DU, DL = oracle.dform(oracle.dist(a1, b), hu), oracle.dform(oracle.dist(a2, b), hl)
+        comb = oracle.dform_combine(DU, DL)
+        for i in range(n + 1):
+            prev = -1
+            for w in range(hu + hl + 1):
+                terms = [(int(DL[DU[i, k], w - k]), k) for k in range(min(w, hu) + 1)
+                         if w - k <= hl and DU[i, k] != INF]
+                best = min(terms)[0] if terms else INF
+                assert best == comb[i, w]
+                if best == INF:
+                    continue
+                k = min(k for v, k in terms if v == best)
+                assert k >= prev
+                prev = k
+
+
 def test_dform_roundtrip():
     rng = np.random.default_rng(9)
     a, b = inputs.random_pair(rng, 6, 15)
