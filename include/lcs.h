@@ -309,9 +309,12 @@ lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b
                      int64_t *out_len_device, void *stream);
 
 /* lcs_solve on HOST buffers: copies a and b to the device, runs the whole
- * path, copies the requested outputs back (dist_host: (n+1) x ld in dtype,
- * lcs_host: cap bytes) and writes *out_len_host.  Host buffers should be
- * pinned for full copy speed (pageable memory works, slower).  Synchronous.
+ * path, returns the requested outputs (dist_host: (n+1) x ld in dtype;
+ * lcs_host: cap bytes, of which the first *out_len_host hold the LCS) and
+ * writes *out_len_host.  A pinned dist_host that the device can address
+ * (16-byte aligned rows) is written by the root merge directly, while the
+ * traceback runs; any other dist_host is filled by a copy from device
+ * staging (pageable memory works, slower).  Synchronous.
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW. */
 lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,
                           const uint8_t *b_host, int64_t n, lcs_dtype dtype,

@@ -170,6 +170,13 @@ struct lcs_ctx {
     size_t batch_bytes = 0;
     std::vector<BatchLane> free_lanes;    // streams/events of released batches
     cudaMemPool_t mempool = nullptr;      // batches' device memory (stream ordered, no device sync)
+    // solve_device: the root merge group beside the traceback
+    cudaStream_t root_side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_root = nullptr;
+    // lcs_solve_host: DIST copied on a side stream while the traceback runs
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_dist = nullptr, ev_copied = nullptr;
+    int64_t *host_hdr = nullptr;          // pinned: error word and length, read once per call
     // CUDA-graph replay of lcs_solve (lcs_set_graphs)
     bool graphs = false;
     cudaStream_t cap_stream = nullptr;    // private stream the solve is captured on
@@ -533,9 +540,12 @@ lcs_status check_dense(lcs_ctx *ctx, const void *p, int64_t n, int64_t ld, int d
 int api_dt(lcs_dtype d) { return d == LCS_I16 ? DT_I16 : DT_I32; }
 
 // The whole hot path on device buffers (see lcs_solve in lcs.h).
+// dist_ready (nullable): recorded on st once the dense DIST is complete,
+// before the traceback kernels that follow it.
 lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                         lcs_dtype dtype, void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap,
-                        int32_t *cross, int64_t *len_dev_out, bool need_len, cudaStream_t st) {
+                        int32_t *cross, int64_t *len_dev_out, bool need_len, cudaStream_t st,
+                        cudaEvent_t dist_ready = nullptr) {
     ctx->launches = 0;
     const int rdt = api_dt(dtype);
     if (m < 0 || n < 0) return fail(ctx, LCS_EINVAL, "negative length");
@@ -550,6 +560,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     if ((m > 0 && !a) || (n > 0 && !b)) return fail(ctx, LCS_EINVAL, "a or b is NULL");
     const bool want_tb = out_lcs || cross;
     const bool want_len = need_len || len_dev_out;
+    bool forked = false;                 // the root merge group runs on ctx->root_side
 
     // Degenerate grids: no rows or no columns.
     if (m == 0 || n == 0) {
@@ -559,6 +570,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 1,
                                               nullptr, st));
         }
+        if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, st));
         LCS_CK(ctx, cudaMemsetAsync(len_word(ctx), 0, sizeof(int64_t), st));
         if (len_dev_out) LCS_CK(ctx, cudaMemsetAsync(len_dev_out, 0, sizeof(int64_t), st));
         if (cross) {
@@ -594,6 +606,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             if (P.NT > 1)
                 LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
                                                   nullptr, st));
+            if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, st));
         }
     } else {
         // All strips share one dtype here (heights <= h, h <= 256 -> u8/i16).
@@ -628,6 +641,22 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         int dpx_launch = 0;
         for (const Group &g : P.groups) {
             if (g.root && !dist) continue;
+            // The root merge writes only the dense DIST, which the traceback
+            // does not read (it reads the root's children): with a traceback
+            // to run, the root group goes to a side stream and the traceback
+            // overlaps it.
+            cudaStream_t gs = st;
+            if (g.root && want_tb) {
+                if (!ctx->root_side) {
+                    LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->root_side, cudaStreamNonBlocking));
+                    LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+                    LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_root, cudaEventDisableTiming));
+                }
+                LCS_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+                LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_fork, 0));
+                gs = ctx->root_side;
+                forked = true;
+            }
             MergeParams mp{};
             mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
             mp.njobs = g.count;
@@ -636,10 +665,10 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             mp.dense_K = nullptr;
             mp.const_tiles = 1;
             mp.sigma = (int32_t)sigma0; mp.full = 1;
-            LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
+            LCS_LAUNCHK(ctx, gs, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, gs));
             for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
                 mp.sigma = (int32_t)sg; mp.full = 0;
-                LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
+                LCS_LAUNCHK(ctx, gs, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, gs));
             }
             const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
                            : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
@@ -647,16 +676,19 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 // A zeroed tile counter per launch (zeroed above, once per solve).
                 mp.sched = dpx_launch < kSchedSlots ? sched + dpx_launch : nullptr;
                 ++dpx_launch;
-                LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, launch_tile_dpx(mp, g.out_dt, st));
+                LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                            0.0, launch_tile_dpx(mp, g.out_dt, gs));
             } else {
-                LCS_LAUNCHK(ctx, st, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, st));
+                LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                            0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, gs));
                 ctx->launches++;   // the pair is two kernel launches
             }
-            if (g.root)
-                LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
-                                                  nullptr, st));
+            if (g.root) {
+                LCS_LAUNCHK(ctx, gs, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                                                  nullptr, gs));
+                if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, gs));
+                if (forked) LCS_CK(ctx, cudaEventRecord(ctx->ev_root, gs));
+            }
         }
     }
 
@@ -692,6 +724,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
         if (len_dev_out) LCS_CK(ctx, launch_copy_len(len_word(ctx), len_dev_out, st));
     }
+    if (forked) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));   // join the root group
     ctx->stats.strip_height = P.h;
     ctx->stats.strips = P.S;
     ctx->stats.merges = (int32_t)P.merges.size();
@@ -753,6 +786,13 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     for (auto &r : ctx->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->root_side) cudaStreamDestroy(ctx->root_side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_root) cudaEventDestroy(ctx->ev_root);
+    if (ctx->ev_dist) cudaEventDestroy(ctx->ev_dist);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+    if (ctx->host_hdr) cudaFreeHost(ctx->host_hdr);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return LCS_OK;
@@ -1161,8 +1201,22 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
     LCS_CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const int rdt = api_dt(dtype);
-    const int64_t ldd = dist_host ? ((n + 1) * dt_size(rdt) + 15) / 16 * 16 / dt_size(rdt) : 0;
-    const size_t dist_bytes = dist_host ? align256((size_t)(n + 1) * ldd * dt_size(rdt)) : 0;
+    // Pinned host memory the device can address: the root merge writes the
+    // dense DIST straight into it (over the CPU-GPU link, beside the
+    // traceback), with no staging copy.  Anything else (pageable memory,
+    // rows not 16-byte aligned) goes through device staging and a copy.
+    void *direct = nullptr;
+    if (dist_host) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, dist_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer && aligned16(pa.devicePointer) && (ld * dt_size(rdt)) % 16 == 0)
+            direct = pa.devicePointer;
+        else
+            (void)cudaGetLastError();
+    }
+    const bool staged = dist_host && !direct;
+    const int64_t ldd = staged ? ((n + 1) * dt_size(rdt) + 15) / 16 * 16 / dt_size(rdt) : (direct ? ld : 0);
+    const size_t dist_bytes = staged ? align256((size_t)(n + 1) * ldd * dt_size(rdt)) : 0;
     const size_t a_off = 0, b_off = align256((size_t)m), l_off = b_off + align256((size_t)n);
     const size_t d_off = l_off + align256((size_t)std::max<int64_t>(cap, 1));
     lcs_status s = ensure_io(ctx, d_off + dist_bytes + 256);
@@ -1170,21 +1224,39 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
     char *io = ctx->io;
     if (m) LCS_CK(ctx, cudaMemcpyAsync(io + a_off, a_host, m, cudaMemcpyHostToDevice, st));
     if (n) LCS_CK(ctx, cudaMemcpyAsync(io + b_off, b_host, n, cudaMemcpyHostToDevice, st));
-    void *dd = dist_host ? (void *)(io + d_off) : nullptr;
+    void *dd = direct ? direct : (staged ? (void *)(io + d_off) : nullptr);
     uint8_t *ld_lcs = lcs_host ? reinterpret_cast<uint8_t *>(io + l_off) : nullptr;
-    s = solve_device(ctx, reinterpret_cast<const uint8_t *>(io + a_off), m, reinterpret_cast<const uint8_t *>(io + b_off),
-                     n, dtype, dd, ldd, ld_lcs, cap, nullptr, nullptr, true, st);
-    if (s != LCS_OK) return s;
-    int64_t len = 0;
-    s = read_back(ctx, st, &len);
-    if (s != LCS_OK) return s;
-    if (dist_host) {
-        LCS_CK(ctx, cudaMemcpy2DAsync(dist_host, (size_t)ld * dt_size(rdt), dd, (size_t)ldd * dt_size(rdt),
-                                      (size_t)(n + 1) * dt_size(rdt), (size_t)(n + 1), cudaMemcpyDeviceToHost, st));
+    if (!ctx->side) {
+        LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_dist, cudaEventDisableTiming));
+        LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+        LCS_CK(ctx, cudaMallocHost(&ctx->host_hdr, 64));
     }
-    if (lcs_host && len > 0) LCS_CK(ctx, cudaMemcpyAsync(lcs_host, ld_lcs, (size_t)len, cudaMemcpyDeviceToHost, st));
+    s = solve_device(ctx, reinterpret_cast<const uint8_t *>(io + a_off), m, reinterpret_cast<const uint8_t *>(io + b_off),
+                     n, dtype, dd, ldd, ld_lcs, cap, nullptr, nullptr, true, st, staged ? ctx->ev_dist : nullptr);
+    if (s != LCS_OK) return s;
+    // A staged DIST leaves on the side stream as soon as it is complete,
+    // while the traceback kernels still run; the LCS (cap bytes) and the
+    // error / length words follow the solve on st; one synchronisation.
+    if (staged) {
+        LCS_CK(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_dist, 0));
+        LCS_CK(ctx, cudaMemcpy2DAsync(dist_host, (size_t)ld * dt_size(rdt), dd, (size_t)ldd * dt_size(rdt),
+                                      (size_t)(n + 1) * dt_size(rdt), (size_t)(n + 1), cudaMemcpyDeviceToHost,
+                                      ctx->side));
+        LCS_CK(ctx, cudaEventRecord(ctx->ev_copied, ctx->side));
+    }
+    if (lcs_host && cap > 0) LCS_CK(ctx, cudaMemcpyAsync(lcs_host, ld_lcs, (size_t)cap, cudaMemcpyDeviceToHost, st));
+    LCS_CK(ctx, cudaMemcpyAsync(ctx->host_hdr, ctx->ws, 16, cudaMemcpyDeviceToHost, st));
+    if (staged) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_copied, 0));
     LCS_CK(ctx, cudaStreamSynchronize(st));
-    *out_len_host = len;
+    const int errbits = (int)(ctx->host_hdr[0] & 0xFFFFFFFF);
+    if (errbits) {
+        LCS_CK(ctx, cudaMemset(ctx->ws, 0, 4));
+        if (errbits & ERR_TIMEOUT) return fail(ctx, LCS_ETIMEOUT, "a device-side wait timed out");
+        if (errbits & ERR_OVERFLOW) return fail(ctx, LCS_EOVERFLOW, "a value or the output exceeded its capacity");
+        return fail(ctx, LCS_ECUDA, "device-side consistency check failed");
+    }
+    *out_len_host = ctx->host_hdr[1];
     return LCS_OK;
 }
 

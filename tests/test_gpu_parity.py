@@ -218,18 +218,25 @@ def test_invalid_arguments(ctx):
         B._dtype_of(torch.zeros(1, dtype=torch.float32))
 
 
-def test_solve_host_roundtrip(ctx):
+@pytest.mark.parametrize("host", ["pinned", "pinned_odd_pitch", "pageable", "pinned_i16"])
+def test_solve_host_roundtrip(ctx, host):
+    """Pinned 16-byte-pitch DIST is written by the root merge directly; an
+    odd pitch or pageable memory goes through device staging and a copy."""
     rng = np.random.default_rng(12)
     a, b = inputs.random_pair(rng, 333, 444)
     B.lcs_set_strip_height(ctx, 0)
     ah = torch.from_numpy(a).pin_memory()
     bh = torch.from_numpy(b).pin_memory()
-    dh = torch.zeros((445, 448), dtype=torch.int32).pin_memory()
+    dt = torch.int16 if host == "pinned_i16" else torch.int32
+    ld = 446 if host == "pinned_odd_pitch" else 448
+    dh = torch.full((445, ld), 5, dtype=dt)
+    if host != "pageable":
+        dh = dh.pin_memory()
     lh = torch.zeros(333, dtype=torch.uint8).pin_memory()
     L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh)
     s_want, _ = oracle.traceback(a, b)
     assert L == len(s_want) and bytes(lh[:L].numpy()) == s_want
-    assert np.array_equal(dh[:, :445].numpy(), oracle.dist(a, b))
+    assert np.array_equal(dh[:, :445].numpy().astype(np.int64), oracle_dist(a, b, dt))
 
 
 # ------------------------------------------------------------------ the named workloads
