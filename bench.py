@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-pair16384", action="store_true", help="skip the m = n = 16384 pair measurement")
     ap.add_argument("--plain-pairs", type=int, default=2000)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
@@ -207,6 +208,62 @@ def roofline(profile, peaks, peaks_src, int_peak):
             "frac": achieved / peak, "traffic": traffic, "peak_source": "hbm_gbs of %s" % peaks_src,
             "algorithmic_bytes_per_launch": p["bytes"] / p["launches"],
             "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"]}
+
+
+def pair16384_measure(B, torch, peaks, peaks_src, steps=3):
+    """The m = n = 16384 pair (20 letters, Zipf(1.1)): int16 DIST of the whole
+    grid + length + LCS, autotuned, CUDA-graph replay, timed with CUDA events
+    on the launching stream (its 0.5 GB output and ~10 GB of merge operands
+    exceed L2); the merge tiles' share and HBM roofline from a profiled pass."""
+    from paper_2309_09072_gb300 import inputs
+    a, b = inputs.pair_16384()
+    m, n = len(a), len(b)
+    dev = torch.device("cuda")
+    ctx = B.lcs_create(torch.cuda.current_device(), 0)
+    try:
+        ad = torch.from_numpy(a.copy()).to(dev)
+        bd = torch.from_numpy(b.copy()).to(dev)
+        ld = ((n + 1) * 2 + 15) // 16 * 16 // 2
+        dist = torch.empty((n + 1, ld), dtype=torch.int16, device=dev)
+        lcs = torch.empty(min(m, n), dtype=torch.uint8, device=dev)
+        ln = torch.empty(1, dtype=torch.int64, device=dev)
+        tuned = B.lcs_autotune(ctx, ad, bd, dist=dist, out_lcs=lcs)
+        B.lcs_set_graphs(ctx, True)
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(2):
+            B.lcs_solve(ctx, ad, bd, dist=dist, out_lcs=lcs, out_len=ln, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.lcs_sync(ctx, stream)
+        e0.record(stream)
+        for _ in range(steps):
+            B.lcs_solve(ctx, ad, bd, dist=dist, out_lcs=lcs, out_len=ln, stream=stream)
+        e1.record(stream)
+        B.lcs_sync(ctx, stream)
+        ms = e0.elapsed_time(e1) / steps
+        B.lcs_set_profiling(ctx, True)
+        B.lcs_solve(ctx, ad, bd, dist=dist, out_lcs=lcs, out_len=ln, stream=stream)
+        B.lcs_sync(ctx, stream)
+        profile = B.lcs_get_profile(ctx)
+        B.lcs_set_profiling(ctx, False)
+        stats = B.lcs_get_stats(ctx)
+        mt = profile.get("merge_tile")
+        merge = None
+        if mt:
+            per = mt["ms"] / mt["launches"]
+            achieved = mt["bytes"] / mt["launches"] / (per * 1e-3) / 1e9
+            merge = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "peak_source": "hbm_gbs of %s" % peaks_src,
+                     "algorithmic_bytes_per_launch": mt["bytes"] / mt["launches"], "ms_per_launch": per,
+                     "launches": mt["launches"]}
+        return {"workload": "single pair m=n=16384, 20 letters Zipf(1.1): int16 DIST of the whole grid + LCS "
+                            "length + leftmost-argmax LCS", "value": m * n / (ms * 1e-3) / 1e9, "unit": "GCUPS",
+                "ms_per_step": ms, "steps": steps, "strip_height": stats["strip_height"],
+                "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
+                "lcs_length": int(ln.item()), "peak_workspace_bytes": stats["peak_workspace_bytes"],
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
+                "merge_roofline": merge}
+    finally:
+        B.lcs_destroy(ctx)
 
 
 def batched_measure(B, torch, plain_pairs, reps=3):
@@ -413,6 +470,8 @@ def run_ours(args):
             "kernels_steps": prof_steps,
             "lcs_length": L, "workspace_bytes": stats["peak_workspace_bytes"]}
     B.lcs_destroy(ctx)
+    if rank == 0 and not args.no_pair16384:
+        line["pair_16384"] = pair16384_measure(B, torch, peaks, peaks_src)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_measure(B, torch, args.plain_pairs)
     if rank == 0 and args.serve_seconds > 0:
