@@ -265,7 +265,8 @@ def test_pair_4096(ctx, variant):
 
 
 def test_pair_16384_sampled(ctx):
-    """m = n = 16384, 20 letters Zipf(1.1), int16 DIST: sampled rows, length, LCS."""
+    """m = n = 16384, 20 letters Zipf(1.1), int16 DIST: 64 seeded rows plus the
+    tile-boundary rows, element by element; length; LCS."""
     a, b = inputs.pair_16384()
     n = len(b)
     B.lcs_set_strip_height(ctx, 0)
@@ -275,7 +276,8 @@ def test_pair_16384_sampled(ctx):
     B.lcs_solve(ctx, dev(a), dev(b), dist=d, out_lcs=out, out_len=ln)
     B.lcs_sync(ctx)
     L = int(ln.item())
-    rows = np.array([0, 1, 8191, 16320, 16384], dtype=np.int64)
+    rows = np.unique(np.concatenate([[0, 1, 63, 64, 8191, 16320, 16383, 16384],
+                                     np.random.default_rng(16384).integers(0, n + 1, 64)])).astype(np.int64)
     got = d[torch.from_numpy(rows).cuda(), : n + 1].cpu().numpy().astype(np.int64)
     want = oracle.dist_rows(a, b, rows).astype(np.int64)
     want[want == np.iinfo(np.int32).min] = np.iinfo(np.int16).min
