@@ -60,12 +60,29 @@ def workload(variant, rank):
     return a, b
 
 
-def config_dict(variant, m, n, h, merge_kernel, graphs):
+def config_dict(variant, m, n):
+    """The workload, the same for both arms."""
     return {"workload": "single pair m=n=4096, ACGT %s: int32 DIST of the whole grid + LCS length + "
                         "leftmost-argmax LCS" % variant,
-            "m": m, "n": n, "variant": variant, "dist_dtype": "int32", "strip_height": h,
-            "merge_kernel": {1: "exact", 2: "dpx"}.get(merge_kernel, "auto"), "cuda_graphs": graphs,
+            "m": m, "n": n, "variant": variant, "dist_dtype": "int32",
             "l2": "flushed between steps (256 MiB write outside the timed events)"}
+
+
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over the ranks of the process group (x itself for
+    one rank): the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gcups(world, m, n, steps, seconds):
+    """Whole-job throughput: every rank solves `steps` pairs of m x n cells,
+    over the slowest rank's time."""
+    return world * m * n * steps / seconds / 1e9
 
 
 # ------------------------------------------------------------------ clocks
@@ -149,7 +166,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": config_dict(args.variant, m, n, 0), "impl": "reference",
+            "config": config_dict(args.variant, m, n), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "per step: oracle DIST on every %dth row (extrapolated to all rows) + "
                                        "full traceback" % stride},
@@ -429,11 +446,8 @@ def run_ours(args):
     B.lcs_sync(ctx, stream)
     profile = B.lcs_get_profile(ctx)
     B.lcs_set_profiling(ctx, False)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * m * n * args.steps / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = aggregate_gcups(world, m, n, args.steps, total_ms * 1e-3)
 
     # End to end through the public host API: H2D of a, b and D2H of DIST,
     # the LCS and the length every step.
@@ -450,11 +464,8 @@ def run_ours(args):
         L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh, stream=stream)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * m * n * args.e2e_steps / e2e_s / 1e9, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": aggregate_gcups(world, m, n, args.e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": m + n, "d2h_bytes_per_step": (n + 1) * (n + 1) * 4 + L + 16,
            "steps": args.e2e_steps, "api": "lcs_solve_host (pinned host buffers)"}
 
@@ -462,7 +473,10 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": config_dict(args.variant, m, n, stats["strip_height"], tuned["merge_kernel"], graphs),
+            "config": config_dict(args.variant, m, n),
+            "tuning": {"strip_height": stats["strip_height"], "cuda_graphs": graphs,
+                       "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
+                       "chosen_by": "lcs_autotune" if args.strip_height == 0 else "--strip-height"},
             "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
             "roofline": roofline(profile, peaks, peaks_src, int_peak),
             "clocks": clock_info,

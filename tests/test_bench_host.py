@@ -1,0 +1,88 @@
+"""Host logic of bench.py that needs no GPU: the reference arm's JSON line
+(plain and under torchrun, where only rank 0 reports) and the multi-rank
+reduction of the timing over a world_size-2 gloo process group."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _check_reference_line(line):
+    d = json.loads(line)
+    assert d["impl"] == "reference"
+    assert d["metric"] and d["unit"] == "GCUPS" and d["value"] > 0
+    assert d["config"]["m"] == 4096 and d["config"]["n"] == 4096
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    return d
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    _check_reference_line(lines[0])
+
+
+def test_reference_arm_under_torchrun():
+    """Two ranks: rank 0 prints the one line, rank 1 exits 0 without work."""
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+                        os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    assert _check_reference_line(lines[0])["n_gpus"] == 2
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # Rank r took (r + 1) * 10 ms for its steps: the job's time is the slowest rank's.
+        t = bench.max_over_ranks((rank + 1) * 0.010, world)
+        q.put((rank, t, bench.aggregate_gcups(world, 4096, 4096, 5, t)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, v in got:
+        assert t == pytest.approx(0.020)
+        assert v == pytest.approx(2 * 4096 * 4096 * 5 / 0.020 / 1e9)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(0.5, 1) == 0.5
+    assert bench.aggregate_gcups(1, 10, 10, 2, 1.0) == pytest.approx(2e-7)
