@@ -160,28 +160,29 @@ __global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel
             const uint32_t bcur = bnext;
             bnext = (blk + 32 + lane < n) ? pr.b[blk + 32 + lane] : 0u;
             const int cnt = (int)min((int64_t)32, n - blk);
+#pragma unroll 2
             for (int t = 0; t < cnt; ++t) {
                 const uint8_t ch = (uint8_t)__shfl_sync(0xFFFFFFFFu, bcur, t);
                 uint32_t M[WPL], s[WPL];
                 masks(ch, M);
                 // This lane's words of V + (V & M) with no carry in: generate
                 // and propagate of the lane.
-                uint32_t carry = 0u;
-                bool ones = true;
+                // This lane's words of V + (V & M) with no carry in (one
+                // add-with-carry chain): generate and propagate of the lane.
+                uint32_t u[WPL];
 #pragma unroll
-                for (int k = 0; k < WPL; ++k) {
-                    const uint64_t sum = (uint64_t)V[k] + (uint64_t)(V[k] & M[k]) + carry;
-                    s[k] = (uint32_t)sum;
-                    carry = (uint32_t)(sum >> 32);
-                    ones = ones && s[k] == 0xFFFFFFFFu;
-                }
-                uint32_t cin = (lane_carries(carry != 0u, ones) >> lane) & 1u;
+                for (int k = 0; k < WPL; ++k) u[k] = V[k] & M[k];
+                const uint32_t carry = addn_cin<WPL>(s, V, u, 0u);
+                // below[k]: every word under k is all ones, so a carry into
+                // the lane reaches word k (computed while the ballots run).
+                uint32_t below[WPL];
+                below[0] = 1u;
 #pragma unroll
-                for (int k = 0; k < WPL; ++k) {
-                    const uint32_t sum = s[k] + cin;
-                    cin = (cin != 0u && sum == 0u) ? 1u : 0u;
-                    V[k] = sum | (V[k] & ~M[k]);
-                }
+                for (int k = 1; k < WPL; ++k) below[k] = below[k - 1] & (s[k - 1] == 0xFFFFFFFFu ? 1u : 0u);
+                const bool ones = (below[WPL - 1] & (s[WPL - 1] == 0xFFFFFFFFu ? 1u : 0u)) != 0u;
+                const uint32_t cin = (lane_carries(carry != 0u, ones) >> lane) & 1u;
+#pragma unroll
+                for (int k = 0; k < WPL; ++k) V[k] = (s[k] + (cin & below[k])) | (V[k] & ~M[k]);
                 if (want) store_col(blk + t + 1);
             }
         }

@@ -1261,14 +1261,19 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
 }
 
 // ----------------------------------------------------------------------------- batches
+// Pairs with more rows than this that want their string take the tall path
+// (batch_big.cu) instead of the one-warp walk.
+constexpr int64_t kBatchBigRows = 4096;
+
 lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, uint64_t *ticket_out) {
     if (!ctx || !ticket_out || count < 0 || (count > 0 && !pairs)) return LCS_EINVAL;
     *ticket_out = 0;
     LCS_CK(ctx, cudaSetDevice(ctx->device));
     const int64_t max_rows = batch_max_rows();
     // Layout of the batch's device block.
-    int64_t n_small = 0, str_bytes = 0, scr_words = 0;
+    int64_t n_small = 0, n_big = 0, str_bytes = 0, scr_words = 0;
     std::vector<int64_t> str_off(count, -1), scr_off(count, 0);
+    std::vector<char> big(count, 0);
     for (int64_t q = 0; q < count; ++q) {
         const lcs_pair &pr = pairs[q];
         if (pr.m < 0 || pr.n < 0 || (pr.m > 0 && !pr.a) || (pr.n > 0 && !pr.b))
@@ -1282,11 +1287,19 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         if (pr.m <= max_rows) {
             ++n_small;
             if (want && pr.m > 0 && pr.n > 0) {
-                // (n+1) column words per row word, then (n+1) x (words+1)
-                // 16-bit counts (batch.cu), rounded to 16 bytes.
                 const int64_t wu = (pr.m + 31) / 32;
                 scr_off[q] = scr_words;
-                scr_words += ((pr.n + 1) * wu + ((pr.n + 1) * (wu + 1) + 1) / 2 + 3) / 4 * 4;
+                if (pr.m > kBatchBigRows) {
+                    // Tall pair (batch_big.cu): forward and backward column
+                    // vectors, then m + 1 cross vertices.
+                    big[q] = 1;
+                    ++n_big;
+                    scr_words += (2 * (pr.n + 1) * wu + pr.m + 1 + 3) / 4 * 4;
+                } else {
+                    // (n+1) column words per row word, then (n+1) x (words+1)
+                    // 16-bit counts (batch.cu), rounded to 16 bytes.
+                    scr_words += ((pr.n + 1) * wu + ((pr.n + 1) * (wu + 1) + 1) / 2 + 3) / 4 * 4;
+                }
             }
         }
     }
@@ -1295,7 +1308,9 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     const size_t o_lens = align256(o_order + sizeof(int32_t) * std::max<int64_t>(1, count));
     const size_t o_err = align256(o_lens + sizeof(int64_t) * std::max<int64_t>(1, count));
     const size_t o_str = align256(o_err + sizeof(int));
-    const size_t o_scr = align256(o_str + (size_t)std::max<int64_t>(1, str_bytes));
+    const size_t o_big = align256(o_str + (size_t)std::max<int64_t>(1, str_bytes));
+    const size_t o_blens = align256(o_big + sizeof(BatchPair) * std::max<int64_t>(1, n_big));
+    const size_t o_scr = align256(o_blens + sizeof(int32_t) * std::max<int64_t>(1, n_big));
     const size_t total = align256(o_scr + (size_t)scr_words * 4);
     if (ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes + total > ctx->budget)
         return fail(ctx, LCS_EAGAIN, "batch does not fit the budget now");
@@ -1355,7 +1370,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         cls_begin[c] = (int64_t)hp.size();
         for (int64_t q = 0; q < count; ++q) {
             const lcs_pair &pr = pairs[q];
-            if (pr.m > max_rows || batch_words_per_lane(pr.m) != wpl) continue;
+            if (pr.m > max_rows || big[q] || batch_words_per_lane(pr.m) != wpl) continue;
             BatchPair b{};
             b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
             b.str_off = str_off[q] < 0 ? 0 : str_off[q];
@@ -1371,6 +1386,25 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         });
     }
     cls_begin[kBatchClasses] = (int64_t)hp.size();
+    // Tall pairs that want their string, by words-per-lane class (8, 16).
+    std::vector<BatchPair> hb;
+    int64_t big_begin[3] = {0, 0, 0}, big_max_n[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+        big_begin[g] = (int64_t)hb.size();
+        for (int64_t q = 0; q < count; ++q) {
+            const lcs_pair &pr = pairs[q];
+            if (!big[q] || batch_words_per_lane(pr.m) != (8 << g)) continue;
+            BatchPair b{};
+            b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
+            b.str_off = str_off[q];
+            b.scratch_off = scr_off[q];
+            b.len_out = t.d_lens + q;
+            b.want = 2;
+            hb.push_back(b);
+            big_max_n[g] = std::max(big_max_n[g], pr.n);
+        }
+    }
+    big_begin[2] = (int64_t)hb.size();
     lcs_status s = LCS_OK;
     do {
         if (cudaEventRecord(t.lane.ev_start, st) != cudaSuccess ||
@@ -1391,38 +1425,74 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             if (ps == LCS_ECUDA) s = ps;
         }
         if (s != LCS_OK) break;
-        if (!hp.empty()) {
-            if (cudaMemcpyAsync(t.dev + o_pairs, hp.data(), sizeof(BatchPair) * hp.size(), cudaMemcpyHostToDevice,
-                                st) != cudaSuccess ||
-                cudaMemcpyAsync(t.dev + o_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
-                                st) != cudaSuccess) {
-                s = fail(ctx, LCS_ECUDA, "batch descriptors");
+        uint32_t *scr = reinterpret_cast<uint32_t *>(t.dev + o_scr);
+        if (!hp.empty() &&
+            (cudaMemcpyAsync(t.dev + o_pairs, hp.data(), sizeof(BatchPair) * hp.size(), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess ||
+             cudaMemcpyAsync(t.dev + o_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+                             st) != cudaSuccess)) {
+            s = fail(ctx, LCS_ECUDA, "batch descriptors");
+            break;
+        }
+        if (!hb.empty()) {
+            if (cudaMemcpyAsync(t.dev + o_big, hb.data(), sizeof(BatchPair) * hb.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+                s = fail(ctx, LCS_ECUDA, "batch tall descriptors");
                 break;
             }
-            // The classes run side by side, each on a stream forked from
-            // the batch's and joined back before ev_done.
-            if (cudaEventRecord(t.lane.ev_fork, st) != cudaSuccess) {
-                s = fail(ctx, LCS_ECUDA, "batch fork");
-                break;
-            }
-            for (int c = 0; c < kBatchClasses && s == LCS_OK; ++c) {
-                const int64_t k0 = cls_begin[c], k1 = cls_begin[c + 1];
-                if (k1 == k0) continue;
-                BatchParams bp{};
-                bp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_pairs) + k0;
-                bp.order = reinterpret_cast<const int32_t *>(t.dev + o_order) + k0;
-                bp.count = k1 - k0;
-                bp.scratch = reinterpret_cast<uint32_t *>(t.dev + o_scr);
-                bp.strings = t.d_strings;
-                bp.err = t.d_err;
-                if (cudaStreamWaitEvent(t.lane.aux[c], t.lane.ev_fork, 0) != cudaSuccess ||
-                    launch_batch_strip(bp, 2 << c, t.lane.aux[c]) != cudaSuccess ||
-                    cudaEventRecord(t.lane.ev_join[c], t.lane.aux[c]) != cudaSuccess ||
-                    cudaStreamWaitEvent(st, t.lane.ev_join[c], 0) != cudaSuccess)
-                    s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
+            for (const BatchPair &b : hb) {
+                const int64_t wu = (b.m + 31) / 32;
+                // Cross vertices start above any column (0x7F7F7F7F > n).
+                if (cudaMemsetAsync(scr + b.scratch_off + 2 * wu * (b.n + 1), 0x7F, sizeof(int32_t) * (b.m + 1), st) !=
+                    cudaSuccess) {
+                    s = fail(ctx, LCS_ECUDA, "batch tall setup");
+                    break;
+                }
             }
             if (s != LCS_OK) break;
         }
+        // The classes run side by side, each on a stream forked from the
+        // batch's; the tall pairs' kernels run on the batch's stream beside
+        // them; the classes join back before ev_done.
+        if (cudaEventRecord(t.lane.ev_fork, st) != cudaSuccess) {
+            s = fail(ctx, LCS_ECUDA, "batch fork");
+            break;
+        }
+        bool joined[kBatchClasses] = {false, false, false, false};
+        for (int c = 0; c < kBatchClasses && s == LCS_OK; ++c) {
+            const int64_t k0 = cls_begin[c], k1 = cls_begin[c + 1];
+            if (k1 == k0) continue;
+            BatchParams bp{};
+            bp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_pairs) + k0;
+            bp.order = reinterpret_cast<const int32_t *>(t.dev + o_order) + k0;
+            bp.count = k1 - k0;
+            bp.scratch = scr;
+            bp.strings = t.d_strings;
+            bp.err = t.d_err;
+            if (cudaStreamWaitEvent(t.lane.aux[c], t.lane.ev_fork, 0) != cudaSuccess ||
+                launch_batch_strip(bp, 2 << c, t.lane.aux[c]) != cudaSuccess ||
+                cudaEventRecord(t.lane.ev_join[c], t.lane.aux[c]) != cudaSuccess)
+                s = fail(ctx, LCS_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(cudaGetLastError()));
+            else
+                joined[c] = true;
+        }
+        for (int g = 0; g < 2 && s == LCS_OK; ++g) {
+            if (big_begin[g + 1] == big_begin[g]) continue;
+            BigParams gp{};
+            gp.pairs = reinterpret_cast<const BatchPair *>(t.dev + o_big) + big_begin[g];
+            gp.count = big_begin[g + 1] - big_begin[g];
+            gp.max_n = big_max_n[g];
+            gp.scratch = scr;
+            gp.lens = reinterpret_cast<int32_t *>(t.dev + o_blens) + big_begin[g];
+            gp.strings = t.d_strings;
+            gp.err = t.d_err;
+            if (launch_big(gp, 8 << g, st) != cudaSuccess)
+                s = fail(ctx, LCS_ECUDA, std::string("batch tall kernels: ") + cudaGetErrorString(cudaGetLastError()));
+        }
+        for (int c = 0; c < kBatchClasses; ++c)
+            if (joined[c] && cudaStreamWaitEvent(st, t.lane.ev_join[c], 0) != cudaSuccess && s == LCS_OK)
+                s = fail(ctx, LCS_ECUDA, "batch join");
+        if (s != LCS_OK) break;
         // (The descriptor copies come from pageable host memory, which the
         // runtime stages before cudaMemcpyAsync returns.)
         if (cudaEventRecord(t.lane.ev_done, st) != cudaSuccess) s = fail(ctx, LCS_ECUDA, "batch event");

@@ -268,4 +268,45 @@ __device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t
     return c;
 }
 
+// ------------------------------------------------------------------ multi-word adds with carry in
+// s = x + y + cin (cin 0 or 1) over 4 words as one add-with-carry chain;
+// returns the carry out of the top word.  The carry in enters the chain
+// through the carry flag: cin + 0xFFFFFFFF carries exactly when cin = 1.
+__device__ __forceinline__ uint32_t add4_cin(uint32_t *s, const uint32_t *x, const uint32_t *y, uint32_t cin) {
+    uint32_t c, t;
+    asm("add.cc.u32 %5, %14, -1;\n\t"
+        "addc.cc.u32 %0, %6, %10;\n\t"
+        "addc.cc.u32 %1, %7, %11;\n\t"
+        "addc.cc.u32 %2, %8, %12;\n\t"
+        "addc.cc.u32 %3, %9, %13;\n\t"
+        "addc.u32 %4, 0, 0;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "=r"(t)
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(cin));
+    return c;
+}
+__device__ __forceinline__ uint32_t add2_cin(uint32_t *s, const uint32_t *x, const uint32_t *y, uint32_t cin) {
+    uint32_t c, t;
+    asm("add.cc.u32 %3, %8, -1;\n\t"
+        "addc.cc.u32 %0, %4, %6;\n\t"
+        "addc.cc.u32 %1, %5, %7;\n\t"
+        "addc.u32 %2, 0, 0;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(c), "=r"(t)
+        : "r"(x[0]), "r"(x[1]), "r"(y[0]), "r"(y[1]), "r"(cin));
+    return c;
+}
+// s = x + y + cin over N words (N = 2 or a multiple of 4), blocks of four
+// chained through their carries; returns the carry out.
+template <int N>
+__device__ __forceinline__ uint32_t addn_cin(uint32_t (&s)[N], const uint32_t (&x)[N], const uint32_t (&y)[N],
+                                             uint32_t cin) {
+    static_assert(N == 2 || N % 4 == 0, "words per lane: 2 or a multiple of 4");
+    if constexpr (N == 2) {
+        return add2_cin(s, x, y, cin);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) cin = add4_cin(s + k, x + k, y + k, cin);
+        return cin;
+    }
+}
+
 }  // namespace lcsg

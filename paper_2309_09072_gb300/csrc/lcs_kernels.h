@@ -184,6 +184,21 @@ struct PathParams {
 };
 cudaError_t launch_path(const PathParams &p, cudaStream_t st);
 
+// Tall batch pairs that want their string (batch_big.cu): scratch per pair
+// of 2 * ceil(m/32) * (n+1) words (forward then backward column vectors,
+// word-major) followed by m + 1 ints of cross vertices, set to a value
+// above n before the launch.
+struct BigParams {
+    const BatchPair *pairs;  // the tall pairs of one words-per-lane class
+    int64_t count;
+    int64_t max_n;           // largest n among them
+    uint32_t *scratch;
+    int32_t *lens;           // count ints: the lengths, for the later kernels
+    uint8_t *strings;
+    int *err;
+};
+cudaError_t launch_big(const BigParams &p, int wpl, cudaStream_t st);
+
 // Breakout (D-form) matrices (dform.cu).
 struct DformStripParams {
     const uint8_t *a;      // m letters: strips of h rows (the last one may be shorter)
