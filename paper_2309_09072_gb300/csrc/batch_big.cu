@@ -1,20 +1,23 @@
-// batch_big.cu -- the LCS of a tall pair of a batch without a serial walk.
+// batch_big.cu -- tall pairs of a batch (more than 4096 rows): several warps
+// per sweep, and the LCS without a serial walk.
 //
-// A batch pair with more than 4096 rows that wants its string takes this
-// path instead of the one-warp walk of batch.cu (whose ~m + n dependent
-// steps dominate such a pair).  With F the strip's DP from the source (0, 0)
+// A batch pair with more than 4096 rows takes this path instead of the
+// one-warp kernel of batch.cu: its sweep spreads the vector over several
+// warps, and when it wants its string the one-warp walk (whose ~m + n
+// dependent steps would dominate such a pair) is replaced as follows.  With F the strip's DP from the source (0, 0)
 // and B the DP from the sink (m, n), the vertices on heaviest paths are those
 // with F(r, c) + B(r, c) = L, so the leftmost heaviest path enters row r at
 //     v[r] = min{ c : F(r, c) + B(r, c) = L }            (Sec. II-C),
 // and the step into row r is a match diagonal, marking letter a_r
 // (Sec. II-E), exactly when v[r] > v[r-1] and a_r = b_{v[r]}: the rule of
 // the single-pair leaf (traceback.cu), on one strip of the whole pair.
-//   1. big_sweep_kernel: a warp sweeps the pair forward (a against b) and
+//   1. big_sweep_kernel: a CTA sweeps the pair forward (a against b) and
 //      another backward (reversed a against reversed b), each with the strip
-//      builder's column step and the batch kernel's cross-lane carry
-//      look-ahead, storing every column's vector word-major (word w of
-//      column c at w * (n+1) + c, so that 32 consecutive columns read one
-//      word coalesced).  The forward warp also gives the length.
+//      builder's column step, the vector spread over four warps (carry
+//      look-ahead within and across them), storing every column's vector
+//      word-major (word w of column c at w * (n+1) + c, so that 32
+//      consecutive columns read one word coalesced).  The forward CTA also
+//      gives the length.
 //   2. big_cross_kernel: a lane per column runs down the rows, its count of
 //      ones moving by (forward bit - backward bit); hits are collected as
 //      32-row masks, transposed across the warp, and the smallest column of
@@ -29,43 +32,48 @@ namespace lcsg {
 
 constexpr int kBigLetters = 32;           // distinct letters with a mask table, else direct compares
 
-__device__ __forceinline__ uint32_t big_lane_carries(bool g, bool p, uint32_t &top) {
-    const uint32_t G = __ballot_sync(0xFFFFFFFFu, g), P = __ballot_sync(0xFFFFFFFFu, p);
-    const uint32_t A = G | P;
-    const uint64_t S = (uint64_t)A + G;
-    top = (uint32_t)(S >> 32);                // carry out of the top lane
-    return (uint32_t)S ^ A ^ G;
-}
-
 template <int WPL>
 struct BigCfg {
-    static constexpr int W = 32 * WPL;
+    static constexpr int W = 32 * WPL;                                  // words of the tallest a
+    static constexpr int NW = WPL / 4;                                  // warps per sweep (4 words per lane)
+    static constexpr int WL = WPL / NW;                                 // words per lane
     static constexpr size_t o_msk = 0;                                  // [kBigLetters][W]
     static constexpr size_t o_a = o_msk + (size_t)kBigLetters * W * 4;  // the strip's letters, in sweep order
     static constexpr size_t o_lmap = o_a + (size_t)W * 32;
     static constexpr size_t o_present = o_lmap + 256;
-    static constexpr size_t bytes = (o_present + 32 + 15) / 16 * 16;
+    static constexpr size_t o_xchg = o_present + 32;                    // [2][NW] warp generate/propagate
+    static constexpr size_t bytes = (o_xchg + 2 * NW * 4 + 15) / 16 * 16;
 };
 
-// Block 2q sweeps pair q forward, block 2q + 1 backward (one warp each).
+// Block 2q sweeps pair q forward, block 2q + 1 backward (only for a pair
+// that wants its string).  The m-bit vector is spread over NW warps (4
+// words per lane), lane l of warp w holding words (32 w + l) WL .. + WL - 1.  Within a warp the carries cross the lanes by
+// the look-ahead on two ballots; across the warps each warp publishes its
+// block's generate (carry out with no carry in) and propagate (every word
+// all ones) bits, a named barrier per column, and a warp's carry in is then
+// the carry of the chain of the warps below it.
 template <int WPL>
-__global__ void __launch_bounds__(32) big_sweep_kernel(BigParams p) {
+__global__ void __launch_bounds__(BigCfg<WPL>::NW * 32) big_sweep_kernel(BigParams p) {
     pdl_wait_and_release();
     using C = BigCfg<WPL>;
+    constexpr int WL = C::WL, NW = C::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t(*msk)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(smem_raw + C::o_msk);
     uint8_t *sa = smem_raw + C::o_a;
     uint8_t *lmap = smem_raw + C::o_lmap;
     uint32_t *present = reinterpret_cast<uint32_t *>(smem_raw + C::o_present);
-    const int lane = threadIdx.x;
+    uint32_t *xchg = reinterpret_cast<uint32_t *>(smem_raw + C::o_xchg);   // bit 0: generate, bit 1: propagate
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q = blockIdx.x >> 1;
     const bool back = (blockIdx.x & 1) != 0;
     if (q >= p.count) return;
     const BatchPair pr = p.pairs[q];
+    const bool want = pr.want != 0;
+    if (back && !want) return;                   // length only: no backward sweep
     const int m = (int)pr.m;
     const int64_t n = pr.n;
     if (m <= 0 || n <= 0 || m > 32 * C::W) {
-        if (lane == 0 && !back) {
+        if (tid == 0 && !back) {
             pr.len_out[0] = 0;
             if (m > 32 * C::W) set_error(p.err, ERR_BOUNDS);
         }
@@ -74,40 +82,40 @@ __global__ void __launch_bounds__(32) big_sweep_kernel(BigParams p) {
     const int Wu = (m + 31) >> 5;
     uint32_t *vec = p.scratch + pr.scratch_off + (back ? (int64_t)Wu * (n + 1) : 0);
     // Rows in sweep order: the backward sweep takes a reversed.
-    if (lane < 8) present[lane] = 0u;
-    __syncwarp();
-    for (int r = lane; r < m; r += 32) {
+    if (tid < 8) present[tid] = 0u;
+    __syncthreads();
+    for (int r = tid; r < m; r += blockDim.x) {
         const uint8_t ch = pr.a[back ? m - 1 - r : r];
         sa[r] = ch;
         atomicOr(&present[ch >> 5], 1u << (ch & 31));
     }
-    __syncwarp();
+    __syncthreads();
     int nlet = 0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) nlet += __popc(present[t]);
     const bool table = nlet <= kBigLetters;
     if (table) {
-        for (int c = lane; c < 256; c += 32) {
+        for (int c = tid; c < 256; c += blockDim.x) {
             const uint32_t word = present[c >> 5], bit = 1u << (c & 31);
             int rank = 0;
             for (int t = 0; t < (c >> 5); ++t) rank += __popc(present[t]);
             rank += __popc(word & (bit - 1u));
             lmap[c] = (word & bit) ? (uint8_t)rank : (uint8_t)255;
         }
-        for (int t = lane; t < nlet * C::W; t += 32) (&msk[0][0])[t] = 0u;
-        __syncwarp();
-        for (int r = lane; r < m; r += 32) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
+        for (int t = tid; t < nlet * C::W; t += blockDim.x) (&msk[0][0])[t] = 0u;
+        __syncthreads();
+        for (int r = tid; r < m; r += blockDim.x) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
     }
-    __syncwarp();
-    const int w0 = lane * WPL;
-    auto masks = [&](uint8_t ch, uint32_t (&M)[WPL]) {
+    __syncthreads();
+    const int w0 = (warp * 32 + lane) * WL;      // this lane's first word
+    auto masks = [&](uint8_t ch, uint32_t (&M)[WL]) {
         if (table) {
             const uint8_t k = lmap[ch];
 #pragma unroll
-            for (int t = 0; t < WPL; ++t) M[t] = (k == 255 || w0 + t >= Wu) ? 0u : msk[k][w0 + t];
+            for (int t = 0; t < WL; ++t) M[t] = (k == 255 || w0 + t >= Wu) ? 0u : msk[k][w0 + t];
         } else {
 #pragma unroll
-            for (int t = 0; t < WPL; ++t) {
+            for (int t = 0; t < WL; ++t) {
                 uint32_t mk = 0u;
                 const int r0 = (w0 + t) * 32;
                 for (int b = 0; b < 32 && r0 + b < m; ++b) mk |= (uint32_t)(sa[r0 + b] == ch) << b;
@@ -115,16 +123,18 @@ __global__ void __launch_bounds__(32) big_sweep_kernel(BigParams p) {
             }
         }
     };
-    uint32_t V[WPL];
+    uint32_t V[WL];
 #pragma unroll
-    for (int t = 0; t < WPL; ++t) V[t] = 0xFFFFFFFFu;
+    for (int t = 0; t < WL; ++t) V[t] = 0xFFFFFFFFu;
     auto store = [&](int64_t c) {
+        if (!want) return;
 #pragma unroll
-        for (int t = 0; t < WPL; ++t)
+        for (int t = 0; t < WL; ++t)
             if (w0 + t < Wu) vec[(int64_t)(w0 + t) * (n + 1) + c] = V[t];
     };
     store(0);
     int dist = 0;
+    int par = 0;
     // Column c' of the sweep takes b[c' - 1] forward, b[n - c'] backward.
     auto letter_at = [&](int64_t cc) -> uint32_t { return back ? pr.b[n - cc] : pr.b[cc - 1]; };
     uint32_t bnext = (1 + lane <= n) ? letter_at(1 + lane) : 0u;
@@ -132,31 +142,43 @@ __global__ void __launch_bounds__(32) big_sweep_kernel(BigParams p) {
         const uint32_t bcur = bnext;
         bnext = (blk + 32 + lane <= n) ? letter_at(blk + 32 + lane) : 0u;
         const int cnt = (int)min((int64_t)32, n - blk + 1);
-#pragma unroll 2
         for (int t = 0; t < cnt; ++t) {
             const uint8_t ch = (uint8_t)__shfl_sync(0xFFFFFFFFu, bcur, t);
-            uint32_t M[WPL], s[WPL];
+            uint32_t M[WL], s[WL], u[WL];
             masks(ch, M);
-            uint32_t u[WPL];
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) u[k] = V[k] & M[k];
-            const uint32_t carry = addn_cin<WPL>(s, V, u, 0u);
-            // below[k]: every word under k is all ones, so a carry into the
-            // lane reaches word k (computed while the ballots are in flight).
-            uint32_t below[WPL];
+            for (int k = 0; k < WL; ++k) u[k] = V[k] & M[k];
+            const uint32_t carry = addn_cin<WL>(s, V, u, 0u);
+            uint32_t below[WL];
             below[0] = 1u;
 #pragma unroll
-            for (int k = 1; k < WPL; ++k) below[k] = below[k - 1] & (s[k - 1] == 0xFFFFFFFFu ? 1u : 0u);
-            const bool ones = (below[WPL - 1] & (s[WPL - 1] == 0xFFFFFFFFu ? 1u : 0u)) != 0u;
-            uint32_t top;
-            const uint32_t cin = (big_lane_carries(carry != 0u, ones, top) >> lane) & 1u;
-            dist += (int)top;
+            for (int k = 1; k < WL; ++k) below[k] = below[k - 1] & (s[k - 1] == 0xFFFFFFFFu ? 1u : 0u);
+            const bool ones = (below[WL - 1] & (s[WL - 1] == 0xFFFFFFFFu ? 1u : 0u)) != 0u;
+            const uint32_t G = __ballot_sync(0xFFFFFFFFu, carry != 0u), Pb = __ballot_sync(0xFFFFFFFFu, ones);
+            const uint32_t A = G | Pb;
+            // The warp's generate and propagate, published for the warps above.
+            const uint32_t wg = (uint32_t)(((uint64_t)A + G) >> 32), wp = Pb == 0xFFFFFFFFu ? 1u : 0u;
+            if (lane == 0) xchg[par * NW + warp] = wg | (wp << 1);
+            named_bar_sync(1, NW * 32);
+            uint32_t cw = 0u;                        // carry into this warp
+            uint32_t ctop = 0u;                      // carry out of the whole vector
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) V[k] = (s[k] + (cin & below[k])) | (V[k] & ~M[k]);
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t e = xchg[par * NW + w];
+                const uint32_t cout = (e & 1u) | ((e >> 1) & ctop);
+                if (w == warp) cw = ctop;
+                ctop = cout;
+            }
+            par ^= 1;
+            const uint64_t S = (uint64_t)A + G + cw;
+            const uint32_t cin = (((uint32_t)S ^ A ^ G) >> lane) & 1u;
+            dist += (int)ctop;                       // DIST(i, j) - DIST(i, j-1)
+#pragma unroll
+            for (int k = 0; k < WL; ++k) V[k] = (s[k] + (cin & below[k])) | (V[k] & ~M[k]);
             store(blk + t);
         }
     }
-    if (!back && lane == 0) {
+    if (!back && tid == 0) {
         pr.len_out[0] = dist;                     // DIST(0, n) = LCS(a, b)
         p.lens[q] = dist;
     }
@@ -171,7 +193,7 @@ __global__ void __launch_bounds__(128) big_cross_kernel(BigParams p) {
     const int m = (int)pr.m;
     const int64_t n = pr.n;
     const int64_t grp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (m <= 0 || n <= 0 || grp * 32 > n) return;
+    if (!pr.want || m <= 0 || n <= 0 || grp * 32 > n) return;
     const int Wu = (m + 31) >> 5;
     const uint32_t *fwd = p.scratch + pr.scratch_off;
     const uint32_t *bwd = fwd + (int64_t)Wu * (n + 1);
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(1024) big_marks_kernel(BigParams p) {
     const BatchPair pr = p.pairs[q];
     const int m = (int)pr.m;
     const int64_t n = pr.n;
-    if (m <= 0 || n <= 0) return;
+    if (!pr.want || m <= 0 || n <= 0) return;
     const int Wu = (m + 31) >> 5;
     const int32_t *v = reinterpret_cast<const int32_t *>(p.scratch + pr.scratch_off + 2 * (int64_t)Wu * (n + 1));
     uint8_t *str = p.strings + pr.str_off;
@@ -273,12 +295,12 @@ cudaError_t launch_big(const BigParams &p, int wpl, cudaStream_t st) {
         auto k = big_sweep_kernel<8>;
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BigCfg<8>::bytes)) != cudaSuccess)
             return e;
-        if ((e = launch_pdl(k, dim3((unsigned)(2 * p.count)), dim3(32), BigCfg<8>::bytes, st, p)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k, dim3((unsigned)(2 * p.count)), dim3(BigCfg<8>::NW * 32), BigCfg<8>::bytes, st, p)) != cudaSuccess) return e;
     } else if (wpl == 16) {
         auto k = big_sweep_kernel<16>;
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BigCfg<16>::bytes)) != cudaSuccess)
             return e;
-        if ((e = launch_pdl(k, dim3((unsigned)(2 * p.count)), dim3(32), BigCfg<16>::bytes, st, p)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k, dim3((unsigned)(2 * p.count)), dim3(BigCfg<16>::NW * 32), BigCfg<16>::bytes, st, p)) != cudaSuccess) return e;
     } else {
         return cudaErrorInvalidValue;
     }

@@ -1261,8 +1261,8 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
 }
 
 // ----------------------------------------------------------------------------- batches
-// Pairs with more rows than this that want their string take the tall path
-// (batch_big.cu) instead of the one-warp walk.
+// Pairs with more rows than this take the tall path (batch_big.cu): a sweep
+// over several warps, and for the string no one-warp walk.
 constexpr int64_t kBatchBigRows = 4096;
 
 lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, uint64_t *ticket_out) {
@@ -1286,20 +1286,22 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         }
         if (pr.m <= max_rows) {
             ++n_small;
-            if (want && pr.m > 0 && pr.n > 0) {
+            if (pr.m > kBatchBigRows && pr.n > 0) {
+                // Tall pair (batch_big.cu); with its string: forward and
+                // backward column vectors, then m + 1 cross vertices.
+                big[q] = 1;
+                ++n_big;
+                if (want) {
+                    const int64_t wu = (pr.m + 31) / 32;
+                    scr_off[q] = scr_words;
+                    scr_words += (2 * (pr.n + 1) * wu + pr.m + 1 + 3) / 4 * 4;
+                }
+            } else if (want && pr.m > 0 && pr.n > 0) {
+                // (n+1) column words per row word, then (n+1) x (words+1)
+                // 16-bit counts (batch.cu), rounded to 16 bytes.
                 const int64_t wu = (pr.m + 31) / 32;
                 scr_off[q] = scr_words;
-                if (pr.m > kBatchBigRows) {
-                    // Tall pair (batch_big.cu): forward and backward column
-                    // vectors, then m + 1 cross vertices.
-                    big[q] = 1;
-                    ++n_big;
-                    scr_words += (2 * (pr.n + 1) * wu + pr.m + 1 + 3) / 4 * 4;
-                } else {
-                    // (n+1) column words per row word, then (n+1) x (words+1)
-                    // 16-bit counts (batch.cu), rounded to 16 bytes.
-                    scr_words += ((pr.n + 1) * wu + ((pr.n + 1) * (wu + 1) + 1) / 2 + 3) / 4 * 4;
-                }
+                scr_words += ((pr.n + 1) * wu + ((pr.n + 1) * (wu + 1) + 1) / 2 + 3) / 4 * 4;
             }
         }
     }
@@ -1396,10 +1398,10 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             if (!big[q] || batch_words_per_lane(pr.m) != (8 << g)) continue;
             BatchPair b{};
             b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
-            b.str_off = str_off[q];
+            b.str_off = str_off[q] < 0 ? 0 : str_off[q];
             b.scratch_off = scr_off[q];
             b.len_out = t.d_lens + q;
-            b.want = 2;
+            b.want = str_off[q] >= 0 ? 1 : 0;
             hb.push_back(b);
             big_max_n[g] = std::max(big_max_n[g], pr.n);
         }
@@ -1441,6 +1443,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
                 break;
             }
             for (const BatchPair &b : hb) {
+                if (!b.want) continue;
                 const int64_t wu = (b.m + 31) / 32;
                 // Cross vertices start above any column (0x7F7F7F7F > n).
                 if (cudaMemsetAsync(scr + b.scratch_off + 2 * wu * (b.n + 1), 0x7F, sizeof(int32_t) * (b.m + 1), st) !=

@@ -273,24 +273,26 @@ __device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t
 // returns the carry out of the top word.  The carry in enters the chain
 // through the carry flag: cin + 0xFFFFFFFF carries exactly when cin = 1.
 __device__ __forceinline__ uint32_t add4_cin(uint32_t *s, const uint32_t *x, const uint32_t *y, uint32_t cin) {
-    uint32_t c, t;
-    asm("add.cc.u32 %5, %14, -1;\n\t"
-        "addc.cc.u32 %0, %6, %10;\n\t"
-        "addc.cc.u32 %1, %7, %11;\n\t"
-        "addc.cc.u32 %2, %8, %12;\n\t"
-        "addc.cc.u32 %3, %9, %13;\n\t"
-        "addc.u32 %4, 0, 0;"
-        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "=r"(t)
+    uint32_t c;
+    asm("{\n\t.reg .u32 ci;\n\t"
+        "add.cc.u32 ci, %13, -1;\n\t"
+        "addc.cc.u32 %0, %5, %9;\n\t"
+        "addc.cc.u32 %1, %6, %10;\n\t"
+        "addc.cc.u32 %2, %7, %11;\n\t"
+        "addc.cc.u32 %3, %8, %12;\n\t"
+        "addc.u32 %4, 0, 0;\n\t}"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c)
         : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(cin));
     return c;
 }
 __device__ __forceinline__ uint32_t add2_cin(uint32_t *s, const uint32_t *x, const uint32_t *y, uint32_t cin) {
-    uint32_t c, t;
-    asm("add.cc.u32 %3, %8, -1;\n\t"
-        "addc.cc.u32 %0, %4, %6;\n\t"
-        "addc.cc.u32 %1, %5, %7;\n\t"
-        "addc.u32 %2, 0, 0;"
-        : "=r"(s[0]), "=r"(s[1]), "=r"(c), "=r"(t)
+    uint32_t c;
+    asm("{\n\t.reg .u32 ci;\n\t"
+        "add.cc.u32 ci, %7, -1;\n\t"
+        "addc.cc.u32 %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
+        "addc.u32 %2, 0, 0;\n\t}"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(c)
         : "r"(x[0]), "r"(x[1]), "r"(y[0]), "r"(y[1]), "r"(cin));
     return c;
 }
