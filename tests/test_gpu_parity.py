@@ -208,6 +208,23 @@ def test_edge_cases(ctx):
     assert s == s_want and np.array_equal(cross, v_want)
 
 
+@pytest.mark.parametrize("h", [0, 64, 256])
+def test_long_horizontal_runs(ctx, h):
+    """Paths whose part in one strip spans more than 1024 columns (a run of
+    letters absent from the strip): the leaf takes its global-memory route."""
+    cases = [
+        (np.full(512, 65, np.uint8), np.concatenate([np.full(3000, 67, np.uint8), np.full(600, 65, np.uint8)])),
+        (np.concatenate([np.full(300, 65, np.uint8), np.full(300, 71, np.uint8)]),
+         np.concatenate([np.full(1500, 67, np.uint8), np.full(200, 65, np.uint8), np.full(1500, 84, np.uint8),
+                         np.full(400, 71, np.uint8)])),
+    ]
+    for a, b in cases:
+        s_want, v_want = oracle.traceback(a, b)
+        s, cross, L = gpu_solve(ctx, a, b, h=h)
+        assert L == len(s_want) and s == s_want
+        assert np.array_equal(cross, v_want)
+
+
 def test_invalid_arguments(ctx):
     a = dev(np.zeros(4, np.uint8))
     d = torch.zeros((5, 7), dtype=torch.int32, device="cuda")     # ld*4 not a multiple of 16
