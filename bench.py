@@ -138,12 +138,34 @@ def oracle_sample(a, b, stride, nthreads=0):
     return (t1 - t0) * (n + 1) / len(rows) + (t2 - t1), threads
 
 
+def length_dp_baseline(a, b):
+    """The oracle's textbook two-row O(mn) DP (length only) on the host: one
+    pair on one core, and one pair per core on all cores at once (the C call
+    releases the GIL)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    m, n = len(a), len(b)
+    oracle.lcs_length(a[:64], b[:64])              # loads the library
+    t0 = time.perf_counter()
+    L = oracle.lcs_length(a, b)
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda _: oracle.lcs_length(a, b), range(cores)))
+    tn = time.perf_counter() - t0
+    return {"kind": "oracle two-row O(mn) DP, length only", "unit": UNIT, "length": L,
+            "one_core": m * n / t1 / 1e9, "all_cores": cores * m * n / tn / 1e9, "cores": cores,
+            "sample": "the whole pair; all cores: one copy of the pair per core"}
+
+
 def cpu_baseline(a, b, stride=4):
     m, n = len(a), len(b)
     t, threads = oracle_sample(a, b, stride)
     return {"value": m * n / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "oracle per-source DIST on every %dth of the %d rows (all host threads), "
-                      "extrapolated to all rows, plus the full O(mn) leftmost traceback" % (stride, n + 1)}
+                      "extrapolated to all rows, plus the full O(mn) leftmost traceback" % (stride, n + 1),
+            "length_dp": length_dp_baseline(a, b)}
 
 
 # ------------------------------------------------------------------ reference arm
