@@ -206,9 +206,9 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def recorded_traffic(kernel_src, summary):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel source changed since those counters were taken."""
+def recorded_counter(kernel_src, summary, key):
+    """A per-launch counter recorded in a committed ncu summary (`key: value`
+    lines), or None when the kernel source changed since it was taken."""
     import hashlib
     try:
         sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
@@ -219,9 +219,14 @@ def recorded_traffic(kernel_src, summary):
                 fields[k.strip()] = v.strip()
         if fields.get("source_sha256_prefix") != sha:
             return None
-        return float(fields["traffic_bytes_per_launch"])
+        return float(fields[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def recorded_traffic(kernel_src, summary):
+    """DRAM bytes per launch from a committed ncu summary (or None)."""
+    return recorded_counter(kernel_src, summary, "traffic_bytes_per_launch")
 
 
 def roofline(profile, peaks, peaks_src, int_peak):
@@ -241,12 +246,20 @@ def roofline(profile, peaks, peaks_src, int_peak):
     achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
     peak = peaks["hbm_gbs"]
     traffic = None
+    out = {}
     if kind == "merge_tile":
-        traffic = recorded_traffic("paper_2309_09072_gb300/csrc/merge.cu", "merge_tile_dpx_pair4096.md")
+        src, summ = "paper_2309_09072_gb300/csrc/merge.cu", "merge_tile_dpx_pair4096.md"
+        traffic = recorded_traffic(src, summ)
+        alu = recorded_counter(src, summ, "alu_pipe_pct_of_peak_active")
+        if alu is not None:
+            # The counted bound is HBM (algorithmic bytes); the kernel itself is
+            # bound by the (max,+) arithmetic: the DPX issue pipe, from ncu.
+            out["measured_bound"] = {"pipe": "alu (DPX max-plus)", "pct_of_peak_active": alu,
+                                     "source": "profiles/" + summ}
     return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": "hbm_gbs of %s" % peaks_src,
             "algorithmic_bytes_per_launch": p["bytes"] / p["launches"],
-            "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"]}
+            "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"], **out}
 
 
 def pair16384_measure(B, torch, peaks, peaks_src, steps=3):
