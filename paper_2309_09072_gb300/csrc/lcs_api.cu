@@ -234,7 +234,11 @@ cudaEvent_t take_event(lcs_ctx *ctx) {
 int prof_begin(lcs_ctx *ctx, cudaStream_t st) {
     if (!ctx->profiling) return -1;
     lcs_ctx::Rec r{0, take_event(ctx), take_event(ctx), 0.0, 0.0};
-    if (!r.e0 || !r.e1) return -1;
+    if (!r.e0 || !r.e1) {                  // out of events: this launch goes untimed
+        if (r.e0) ctx->pool.push_back(r.e0);
+        if (r.e1) ctx->pool.push_back(r.e1);
+        return -1;
+    }
     cudaEventRecord(r.e0, st);
     ctx->recs.push_back(r);
     return (int)ctx->recs.size() - 1;
@@ -847,14 +851,16 @@ lcs_status lcs_autotune(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     cudaStream_t st = (cudaStream_t)stream;
     const int root_dt = api_dt(dtype);
     const std::vector<int64_t> key = tune_key(m, n, root_dt);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(ctx, LCS_ECUDA, cudaGetErrorString(cudaGetLastError()));
+    }
     const int32_t keep_h = ctx->strip_h, keep_mk = ctx->merge_kernel;
     const bool keep_prof = ctx->profiling, keep_graphs = ctx->graphs;
     ctx->profiling = false;
     ctx->graphs = false;
     ctx->tuned.erase(key);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    LCS_CK(ctx, cudaEventCreate(&e0));
-    LCS_CK(ctx, cudaEventCreate(&e1));
     float best_ms = -1.0f;
     int32_t best_h = 0, best_mk = LCS_MERGE_AUTO;
     lcs_status s = LCS_OK;
@@ -910,7 +916,8 @@ lcs_status lcs_get_stats(lcs_ctx *ctx, lcs_stats *out) {
 
 lcs_status lcs_set_profiling(lcs_ctx *ctx, int32_t enable) {
     if (!ctx) return LCS_EINVAL;
-    cudaDeviceSynchronize();
+    LCS_CK(ctx, cudaSetDevice(ctx->device));
+    LCS_CK(ctx, cudaDeviceSynchronize());
     for (auto &r : ctx->recs) { ctx->pool.push_back(r.e0); ctx->pool.push_back(r.e1); }
     ctx->recs.clear();
     ctx->profiling = enable != 0;

@@ -26,7 +26,7 @@ def ctx():
 
 
 def dev(x):
-    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint8)).cuda()
+    return torch.from_numpy(np.array(x, dtype=np.uint8, copy=True)).cuda()
 
 
 def dist_buffer(n, dtype=torch.int32, pad=0):
