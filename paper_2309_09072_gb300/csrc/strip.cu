@@ -23,6 +23,8 @@
 // Once every source of a band has matched all rows of the strip, DIST stays
 // at h for the rest of the band's row, so the band's remaining tiles are
 // written as constants without further column steps.
+#include <type_traits>
+
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
@@ -108,17 +110,23 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
     int d = 0;
     const int r = half * 32 + lane;            // this lane's source is i0 + r, row r of the staged tile
 
+    // Column c of tile J consumes letter b[J T + c - 1]; each lane of the
+    // pair reads one column's letter, one tile ahead, so that the global
+    // load's latency passes behind a tile of column steps.
+    auto letter = [&](int64_t Jt) -> int {
+        const int64_t j = Jt * T + half * 32 + lane;
+        return (Jt < p.NT && j >= 1 && j <= n) ? (int)p.b[j - 1] : -1;
+    };
+    int ch_next = letter(I);
     for (int64_t J = I; J < p.NT; ++J) {
         const int64_t jb = J * T;
-        // Column masks of this tile (each warp of the pair builds half):
-        // column c consumes letter b[jb + c - 1].
+        // Column masks of this tile (each warp of the pair builds half).
         {
             const int c = half * 32 + lane;
-            const int64_t j = jb + c;
-            const bool in = j >= 1 && j <= n;
-            const uint8_t ch = in ? p.b[j - 1] : 0;
+            const int ch = ch_next;
+            ch_next = letter(J + 1);
 #pragma unroll
-            for (int w = 0; w < W; ++w) colm[c * W + w] = in ? masks[ch * W + w] : 0u;
+            for (int w = 0; w < W; ++w) colm[c * W + w] = ch >= 0 ? masks[ch * W + w] : 0u;
         }
         // The masks are complete, and the previous tile has left the stage.
         pair_sync();
@@ -134,24 +142,28 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
                 if (layout == LAYOUT_COL) stage[c * P + r] = v;
                 else stage[r * P + c] = v;
             }
-        } else if (layout == LAYOUT_COL) {
-#pragma unroll 4
-            for (int c = 0; c < cmax; ++c) {
-                uint32_t M[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
-                d += (int)column_step<W>(V, M);
-                stage[c * P + r] = (OutT)d;
-            }
         } else {
-#pragma unroll 4
-            for (int c = 0; c < cmax; ++c) {
-                uint32_t M[W];
+            // Column c + 1's masks load while column c's carry chain runs;
+            // the staging stride is a constant of each layout's loop.
+            auto sweep = [&](auto col_layout) {
+                constexpr int SC = decltype(col_layout)::value ? P : 1, SR = decltype(col_layout)::value ? 1 : P;
+                uint32_t Mn[W];
 #pragma unroll
-                for (int w = 0; w < W; ++w) M[w] = colm[c * W + w];
-                d += (int)column_step<W>(V, M);
-                stage[r * P + c] = (OutT)d;
-            }
+                for (int w = 0; w < W; ++w) Mn[w] = colm[w];
+#pragma unroll 4
+                for (int c = 0; c < cmax; ++c) {
+                    uint32_t M[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) M[w] = Mn[w];
+                    const int cn = c + 1 < cmax ? c + 1 : c;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) Mn[w] = colm[cn * W + w];
+                    d += (int)column_step<W>(V, M);
+                    stage[c * SC + r * SR] = (OutT)d;
+                }
+            };
+            if (layout == LAYOUT_COL) sweep(std::true_type{});
+            else sweep(std::false_type{});
         }
         // Once every source of the band has matched all hs rows, DIST stays
         // hs for the rest of the row: the remaining tiles are constant.
