@@ -181,6 +181,40 @@ def _ld(t) -> int:
     return int(t.stride(0))
 
 
+def _place(t, name: str, device: bool) -> None:
+    if device and not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not device and t.is_cuda:
+        raise ValueError("%s must be a host (CPU) tensor" % name)
+
+
+def _seq(t, name: str, device: bool = True):
+    """A string: contiguous uint8 bytes on the device (or the host)."""
+    import torch
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous uint8 tensor" % name)
+    _place(t, name, device)
+    return _ptr(t), int(t.numel())
+
+
+def _out(t, name: str, dtype, device: bool = True):
+    """An output buffer of one element type, contiguous; None passes through."""
+    if t is None:
+        return None
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor" % (name, str(dtype).replace("torch.", "")))
+    _place(t, name, device)
+    return _ptr(t)
+
+
+def _mat(t, name: str, device: bool = True) -> int:
+    """A DIST / breakout matrix: 2-D, unit column stride; returns ld."""
+    ld = _ld(t)
+    _dtype_of(t)
+    _place(t, name, device)
+    return ld
+
+
 def _check(ctx, status):
     if status != LCS_OK:
         msg = load().lcs_last_error(ctx)
@@ -224,13 +258,15 @@ def lcs_set_graphs(ctx, enable: bool) -> None:
 def lcs_autotune(ctx, a, b, dist=None, out_lcs=None, stream=None) -> dict:
     """Time the candidate strip heights / merge kernels on this call's shape
     and outputs; returns the choice kept for the size bucket."""
+    import torch
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     dtype = _dtype_of(dist) if dist is not None else LCS_I32
-    ld = _ld(dist) if dist is not None else 0
+    ld = _mat(dist, "dist") if dist is not None else 0
     cap = int(out_lcs.numel()) if out_lcs is not None else 0
     h, mk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
-    _check(ctx, load().lcs_autotune(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), dtype, _ptr(dist), ld,
-                                    _ptr(out_lcs), cap, _stream(stream), ctypes.byref(h), ctypes.byref(mk),
-                                    ctypes.byref(ms)))
+    _check(ctx, load().lcs_autotune(ctx, pa, m, pb, n, dtype, _ptr(dist), ld,
+                                    _out(out_lcs, "out_lcs", torch.uint8), cap, _stream(stream), ctypes.byref(h),
+                                    ctypes.byref(mk), ctypes.byref(ms)))
     return {"strip_height": h.value, "merge_kernel": mk.value, "ms": ms.value}
 
 
@@ -270,40 +306,61 @@ def lcs_sync(ctx, stream=None) -> None:
 
 def lcs_strip_dist(ctx, a_strip, b, dist, stream=None) -> None:
     """dist[i, j] = LCS(a_strip, b[i:j]) (dense (n+1) x ld int32/int16)."""
-    _check(ctx, load().lcs_strip_dist(ctx, _ptr(a_strip), int(a_strip.numel()), _ptr(b), int(b.numel()),
-                                      _dtype_of(dist), _ptr(dist), _ld(dist), _stream(stream)))
+    (pa, h), (pb, n) = _seq(a_strip, "a_strip"), _seq(b, "b")
+    ld = _mat(dist, "dist")
+    _check(ctx, load().lcs_strip_dist(ctx, pa, h, pb, n, _dtype_of(dist), _ptr(dist), ld, _stream(stream)))
+
+
+def _merge_args(dist_u, dist_l, dist_out, argmax_out):
+    """(n, ld) of a merge's matrices: one dtype and one ld, on the device."""
+    import torch
+    ld = _mat(dist_u, "dist_u")
+    _mat(dist_l, "dist_l")
+    _mat(dist_out, "dist_out")
+    if dist_l.dtype != dist_u.dtype or dist_out.dtype != dist_u.dtype or dist_l.stride(0) != ld \
+            or dist_out.stride(0) != ld:
+        raise ValueError("dist_u, dist_l and dist_out share one dtype and one ld")
+    if argmax_out is not None:
+        if argmax_out.dtype != torch.int32 or argmax_out.dim() != 2 or argmax_out.stride(1) != 1 \
+                or argmax_out.stride(0) != ld:
+            raise ValueError("argmax_out must be int32 with the matrices' ld")
+        _place(argmax_out, "argmax_out", True)
+    return int(dist_u.shape[0]) - 1, ld
 
 
 def lcs_merge(ctx, dist_u, dist_l, dist_out, argmax_out=None, stream=None) -> None:
     """dist_out[i, j] = max_k dist_u[i, k] + dist_l[k, j]; argmax_out = smallest k."""
-    n = dist_u.shape[0] - 1
-    _check(ctx, load().lcs_merge(ctx, _ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), _ld(dist_u),
+    n, ld = _merge_args(dist_u, dist_l, dist_out, argmax_out)
+    _check(ctx, load().lcs_merge(ctx, _ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), ld,
                                  _ptr(dist_out), _ptr(argmax_out), _stream(stream)))
 
 
 def lcs_merge_static(dist_u, dist_l, dist_out, argmax_out=None, stream=None) -> None:
     """lcs_merge with all scratch in the library's static device array (no
     allocation, n <= 1024, synchronous)."""
-    n = dist_u.shape[0] - 1
-    _check(None, load().lcs_merge_static(_ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), _ld(dist_u),
+    n, ld = _merge_args(dist_u, dist_l, dist_out, argmax_out)
+    _check(None, load().lcs_merge_static(_ptr(dist_u), _ptr(dist_l), n, _dtype_of(dist_u), ld,
                                          _ptr(dist_out), _ptr(argmax_out), _stream(stream)))
 
 
 def lcs_dist(ctx, a, b, dist, stream=None) -> None:
-    _check(ctx, load().lcs_dist(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _dtype_of(dist),
-                                _ptr(dist), _ld(dist), _stream(stream)))
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
+    ld = _mat(dist, "dist")
+    _check(ctx, load().lcs_dist(ctx, pa, m, pb, n, _dtype_of(dist), _ptr(dist), ld, _stream(stream)))
 
 
 def lcs_length(ctx, a, b, stream=None) -> int:
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     out = ctypes.c_int64()
-    _check(ctx, load().lcs_length(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()),
-                                  ctypes.byref(out), _stream(stream)))
+    _check(ctx, load().lcs_length(ctx, pa, m, pb, n, ctypes.byref(out), _stream(stream)))
     return out.value
 
 
 def lcs_traceback(ctx, a, b, out_lcs, stream=None) -> int:
+    import torch
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     out = ctypes.c_int64()
-    _check(ctx, load().lcs_traceback(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(out_lcs),
+    _check(ctx, load().lcs_traceback(ctx, pa, m, pb, n, _out(out_lcs, "out_lcs", torch.uint8),
                                      int(out_lcs.numel()), ctypes.byref(out), _stream(stream)))
     return out.value
 
@@ -312,51 +369,64 @@ def lcs_strip_dform(ctx, a, b, dform, h=None, stream=None) -> None:
     """Breakout matrices of a's strips of h rows (default: one strip of all of
     a) into ``dform``: shape (S, n+1, ldf) or, for one strip, (n+1, ldf);
     int32 or int16."""
-    m = int(a.numel())
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     h = m if h is None else int(h)
+    if dform.dim() not in (2, 3):
+        raise ValueError("dform is (n+1, ldf) or (S, n+1, ldf)")
     d2 = dform if dform.dim() == 2 else dform[0]
+    _mat(d2, "dform")
     if dform.dim() == 3 and dform.stride(0) != (int(b.numel()) + 1) * d2.stride(0):
         raise ValueError("strips of dform must be contiguous (n+1) x ldf blocks")
-    _check(ctx, load().lcs_strip_dform(ctx, _ptr(a), m, h, _ptr(b), int(b.numel()), _dtype_of(d2), _ptr(dform),
-                                       _ld(d2), _stream(stream)))
+    _check(ctx, load().lcs_strip_dform(ctx, pa, m, h, pb, n, _dtype_of(d2), _ptr(dform), _ld(d2),
+                                       _stream(stream)))
 
 
 def lcs_dform_merge(ctx, du, hu, dl, hl, out, stream=None) -> None:
     """Combination of two breakout matrices (rows = top vertices) into ``out``."""
     n = int(du.shape[0]) - 1
-    _check(ctx, load().lcs_dform_merge(ctx, _ptr(du), int(hu), _ld(du), _ptr(dl), int(hl), _ld(dl), n,
-                                       _dtype_of(out), _ptr(out), _ld(out), _stream(stream)))
+    ldu, ldl, ldo = _mat(du, "du"), _mat(dl, "dl"), _mat(out, "out")
+    if du.dtype != out.dtype or dl.dtype != out.dtype:
+        raise ValueError("du, dl and out share one dtype")
+    _check(ctx, load().lcs_dform_merge(ctx, _ptr(du), int(hu), ldu, _ptr(dl), int(hl), ldl, n,
+                                       _dtype_of(out), _ptr(out), ldo, _stream(stream)))
 
 
 def lcs_path(ctx, a, b, path, stream=None) -> int:
     """Vertices of the leftmost heaviest path into ``path`` (int32, shape
     (cap, 2) of (row, col) pairs); returns their number."""
+    import torch
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     out = ctypes.c_int64()
     cap = int(path.numel()) // 2 if path is not None else 0
-    _check(ctx, load().lcs_path(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), _ptr(path), cap,
+    _check(ctx, load().lcs_path(ctx, pa, m, pb, n, _out(path, "path", torch.int32), cap,
                                 ctypes.byref(out), _stream(stream)))
     return out.value
 
 
 def lcs_solve(ctx, a, b, dist=None, out_lcs=None, cross=None, out_len=None, stream=None) -> None:
     """Asynchronous whole path; any output may be None (see lcs.h)."""
+    import torch
+    (pa, m), (pb, n) = _seq(a, "a"), _seq(b, "b")
     dtype = _dtype_of(dist) if dist is not None else LCS_I32
-    ld = _ld(dist) if dist is not None else 0
+    ld = _mat(dist, "dist") if dist is not None else 0
     cap = int(out_lcs.numel()) if out_lcs is not None else 0
-    _check(ctx, load().lcs_solve(ctx, _ptr(a), int(a.numel()), _ptr(b), int(b.numel()), dtype, _ptr(dist), ld,
-                                 _ptr(out_lcs), cap, _ptr(cross), _ptr(out_len), _stream(stream)))
+    _check(ctx, load().lcs_solve(ctx, pa, m, pb, n, dtype, _ptr(dist), ld,
+                                 _out(out_lcs, "out_lcs", torch.uint8), cap, _out(cross, "cross", torch.int32),
+                                 _out(out_len, "out_len", torch.int64), _stream(stream)))
 
 
 def lcs_solve_host(ctx, a_host, b_host, dist_host=None, lcs_host=None, dtype=LCS_I32, stream=None) -> int:
     """Whole path on host (ideally pinned) tensors; returns the LCS length."""
+    import torch
+    (pa, m), (pb, n) = _seq(a_host, "a_host", device=False), _seq(b_host, "b_host", device=False)
     out = ctypes.c_int64()
     if dist_host is not None:
         dtype = _dtype_of(dist_host)
-    ld = _ld(dist_host) if dist_host is not None else 0
+    ld = _mat(dist_host, "dist_host", device=False) if dist_host is not None else 0
     cap = int(lcs_host.numel()) if lcs_host is not None else 0
-    _check(ctx, load().lcs_solve_host(ctx, _ptr(a_host), int(a_host.numel()), _ptr(b_host), int(b_host.numel()),
-                                      dtype, _ptr(dist_host), ld, _ptr(lcs_host), cap, ctypes.byref(out),
-                                      _stream(stream)))
+    _check(ctx, load().lcs_solve_host(ctx, pa, m, pb, n, dtype, _ptr(dist_host), ld,
+                                      _out(lcs_host, "lcs_host", torch.uint8, device=False), cap,
+                                      ctypes.byref(out), _stream(stream)))
     return out.value
 
 
@@ -366,6 +436,8 @@ def lcs_batch_submit(ctx, pairs) -> int:
     arr = (lcs_pair * max(1, len(pairs)))()
     for k, pr in enumerate(pairs):
         a, b = pr[0], pr[1]
+        _seq(a, "a of pair %d" % k)
+        _seq(b, "b of pair %d" % k)
         want = pr[2] if len(pr) > 2 else True
         arr[k].a = a.data_ptr() if a.numel() else None
         arr[k].m = int(a.numel())
