@@ -159,6 +159,51 @@ def length_dp_baseline(a, b):
             "sample": "the whole pair; all cores: one copy of the pair per core"}
 
 
+def pairs_length_dp(pairs, sample):
+    """The oracle's two-row O(mn) DP (length only) over many pairs, spread
+    over all host cores (the C call releases the GIL); largest pairs first,
+    dealt round-robin into chunks so the pool's tail stays short."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    oracle.lcs_length(pairs[0][0][:8], pairs[0][1][:8])      # loads the library
+    cells = sum(len(x) * len(y) for x, y in pairs)
+    order = sorted(range(len(pairs)), key=lambda k: -len(pairs[k][0]) * len(pairs[k][1]))
+    chunks = [order[c::cores * 4] for c in range(cores * 4)]
+
+    def run(chunk):
+        for k in chunk:
+            oracle.lcs_length(pairs[k][0], pairs[k][1])
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(run, chunks))
+    t = time.perf_counter() - t0
+    return {"kind": "oracle two-row O(mn) DP, length only", "unit": UNIT, "value": cells / t / 1e9,
+            "cores": cores, "seconds": t, "pairs": len(pairs), "sample": sample}
+
+
+def workload_baselines(batched, serve_seconds, serve_sample=2000):
+    """Host baselines of the batched and serving workloads (the same seeded
+    pairs the GPU measurements use)."""
+    from paper_2309_09072_gb300 import inputs
+    out = {}
+    if batched:
+        out["batched_length_dp"] = pairs_length_dp(inputs.batch_pairs(), "all 20,000 pairs of the batched workload")
+    if serve_seconds > 0:
+        import oracle
+        _, req = inputs.serving_requests(duration_s=serve_seconds)
+        req = req[:serve_sample]
+        r = pairs_length_dp(req, "the first %d requests of the serving workload" % len(req))
+        big = next(((x, y) for x, y in req if len(x) * len(y) >= 16384 * 16384), None)
+        if big is not None:
+            t0 = time.perf_counter()
+            oracle.lcs_length(big[0], big[1])
+            r["pair_16384_one_core_ms"] = (time.perf_counter() - t0) * 1e3
+        out["serving_length_dp"] = r
+    return out
+
+
 def cpu_baseline(a, b, stride=4):
     m, n = len(a), len(b)
     t, threads = oracle_sample(a, b, stride)
@@ -527,6 +572,7 @@ def run_ours(args):
         line["serving"] = serving_measure(B, torch, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, b)
+        line["cpu_baseline"].update(workload_baselines(not args.no_batched, args.serve_seconds))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
