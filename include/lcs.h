@@ -312,8 +312,9 @@ lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b
  * path, returns the requested outputs (dist_host: (n+1) x ld in dtype;
  * lcs_host: cap bytes, of which the first *out_len_host hold the LCS) and
  * writes *out_len_host.  A pinned dist_host that the device can address
- * (16-byte aligned rows) is written by the root merge directly, while the
- * traceback runs; any other dist_host is filled by a copy from device
+ * (16-byte aligned rows) is written by the kernels directly: its lower
+ * triangle while the tree is built, the rest by the root merge while the
+ * traceback runs.  Any other dist_host is filled by a copy from device
  * staging (pageable memory works, slower).  Synchronous.
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW. */
 lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,

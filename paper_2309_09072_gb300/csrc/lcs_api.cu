@@ -259,6 +259,15 @@ void prof_end(lcs_ctx *ctx, int idx, cudaStream_t st, int kind, double bytes, do
         prof_end(ctx, pi_, st, kind, bytes, ops);                 \
     } while (0)
 
+// The side stream of a solve (the early dense fill, the root merge group)
+// and its fork / join events, created on first use.
+lcs_status ensure_root_side(lcs_ctx *ctx) {
+    if (!ctx->root_side) LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->root_side, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_root) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_root, cudaEventDisableTiming));
+    return LCS_OK;
+}
+
 int auto_strip_height(int64_t m, int64_t n) {
     (void)n;
     if (m <= 256) return (int)std::max<int64_t>(m, 1);
@@ -544,12 +553,14 @@ lcs_status check_dense(lcs_ctx *ctx, const void *p, int64_t n, int64_t ld, int d
 int api_dt(lcs_dtype d) { return d == LCS_I16 ? DT_I16 : DT_I32; }
 
 // The whole hot path on device buffers (see lcs_solve in lcs.h).
-// dist_ready (nullable): recorded on st once the dense DIST is complete,
-// before the traceback kernels that follow it.
+// dist_ready (nullable): recorded once the dense DIST is complete, on the
+// stream that completes it, before the traceback kernels that follow.
+// early_fill: dist is pinned host memory; its lower triangle is filled on
+// the side stream while the merge levels run.
 lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                         lcs_dtype dtype, void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap,
                         int32_t *cross, int64_t *len_dev_out, bool need_len, cudaStream_t st,
-                        cudaEvent_t dist_ready = nullptr) {
+                        cudaEvent_t dist_ready = nullptr, bool early_fill = false) {
     ctx->launches = 0;
     const int rdt = api_dt(dtype);
     if (m < 0 || n < 0) return fail(ctx, LCS_EINVAL, "negative length");
@@ -565,6 +576,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     const bool want_tb = out_lcs || cross;
     const bool want_len = need_len || len_dev_out;
     bool forked = false;                 // the root merge group runs on ctx->root_side
+    bool fill_side = false;              // the dense fill runs on ctx->root_side
 
     // Degenerate grids: no rows or no columns.
     if (m == 0 || n == 0) {
@@ -613,6 +625,27 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, st));
         }
     } else {
+        // The dense DIST's lower triangle outside the diagonal tiles is
+        // written by no merge tile.  When the DIST is pinned host memory
+        // (early_fill), that fill crosses the CPU-GPU link, so it runs on the
+        // side stream from the start, beside the strip builder and the merge
+        // levels, instead of after the root; half the SMs get one block each.
+        // A device DIST is filled after the root merge instead (a few
+        // microseconds of HBM writes, where a concurrent fill measurably
+        // slows the latency-bound strip builder).
+        if (dist && early_fill) {
+            lcs_status ss = ensure_root_side(ctx);
+            if (ss != LCS_OK) return ss;
+            int sms = 0;
+            LCS_CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            LCS_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+            LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_fork, 0));
+            LCS_LAUNCHK(ctx, ctx->root_side, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                        launch_fill_lower(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN,
+                                          std::max(1, sms / 2), ctx->root_side));
+            LCS_CK(ctx, cudaEventRecord(ctx->ev_root, ctx->root_side));
+            fill_side = true;
+        }
         // All strips share one dtype here (heights <= h, h <= 256 -> u8/i16).
         StripParams sp{};
         sp.a = a; sp.m = m; sp.h = P.h; sp.S = P.S; sp.b = b; sp.n = n; sp.NT = P.NT;
@@ -651,11 +684,8 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             // overlaps it.
             cudaStream_t gs = st;
             if (g.root && want_tb) {
-                if (!ctx->root_side) {
-                    LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->root_side, cudaStreamNonBlocking));
-                    LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-                    LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_root, cudaEventDisableTiming));
-                }
+                lcs_status ss = ensure_root_side(ctx);
+                if (ss != LCS_OK) return ss;
                 LCS_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
                 LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_fork, 0));
                 gs = ctx->root_side;
@@ -688,8 +718,16 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 ctx->launches++;   // the pair is two kernel launches
             }
             if (g.root) {
-                LCS_LAUNCHK(ctx, gs, K_FILL, tri_entries(n) * dt_size(rdt), 0.0, launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                if (!fill_side) {
+                    LCS_LAUNCHK(ctx, gs, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                                launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
                                                   nullptr, gs));
+                } else if (!forked) {
+                    // The early fill ran on the side stream: the DIST is
+                    // complete once it has (on the side stream it precedes
+                    // the root group anyway).
+                    LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));
+                }
                 if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, gs));
                 if (forked) LCS_CK(ctx, cudaEventRecord(ctx->ev_root, gs));
             }
@@ -728,7 +766,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
         if (len_dev_out) LCS_CK(ctx, launch_copy_len(len_word(ctx), len_dev_out, st));
     }
-    if (forked) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));   // join the root group
+    if (forked || fill_side) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));   // join the side stream
     ctx->stats.strip_height = P.h;
     ctx->stats.strips = P.S;
     ctx->stats.merges = (int32_t)P.merges.size();
@@ -1240,7 +1278,8 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m, const 
         LCS_CK(ctx, cudaMallocHost(&ctx->host_hdr, 64));
     }
     s = solve_device(ctx, reinterpret_cast<const uint8_t *>(io + a_off), m, reinterpret_cast<const uint8_t *>(io + b_off),
-                     n, dtype, dd, ldd, ld_lcs, cap, nullptr, nullptr, true, st, staged ? ctx->ev_dist : nullptr);
+                     n, dtype, dd, ldd, ld_lcs, cap, nullptr, nullptr, true, st, staged ? ctx->ev_dist : nullptr,
+                     direct != nullptr);
     if (s != LCS_OK) return s;
     // A staged DIST leaves on the side stream as soon as it is complete,
     // while the traceback kernels still run; the LCS (cap bytes) and the

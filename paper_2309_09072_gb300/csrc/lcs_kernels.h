@@ -112,6 +112,12 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int64_t ld, void 
 // `lower`; with `fill_upper` the whole upper triangle (j >= i) gets `upper`.
 cudaError_t launch_fill_dense(void *out, int dtype, int64_t n, int64_t ld, int lower, int upper,
                               int fill_upper, int32_t *K, cudaStream_t st);
+// The lower triangle outside the diagonal tiles (row i, columns
+// [0, 64 floor(i / 64))) set to `lower` with 16-byte stores by `blocks`
+// blocks of 256 threads: the region no merge tile writes, so it can be
+// filled on a side stream while the tree is built.  out and ld * element
+// size must be 16-byte aligned.
+cudaError_t launch_fill_lower(void *out, int dtype, int64_t n, int64_t ld, int lower, int blocks, cudaStream_t st);
 
 // ------------------------------------------------------------- traceback
 struct TbMerge {

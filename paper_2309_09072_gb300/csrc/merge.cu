@@ -693,6 +693,33 @@ __host__ __device__ inline DpxSmem dpx_smem_layout(int out_dt, int cap) {
     return s;
 }
 
+// Rows [0, rows) of an output tile into the caller's dense matrix, entry
+// (x, y) = val(x, y).  A tile whose T columns all exist is written with
+// 16-byte stores (its rows start 16-byte aligned: ld and the column offset
+// are multiples of 16 bytes), which matters when the matrix is pinned host
+// memory written over the CPU-GPU link; the last tile column element-wise.
+template <typename TOut, typename F>
+__device__ __forceinline__ void store_dense_tile(TOut *out, int64_t ld, int64_t ia, int64_t ja, int rows, int cols,
+                                                 F val) {
+    constexpr int E = 16 / (int)sizeof(TOut);   // elements per 16-byte word
+    constexpr int WPR = T / E;                  // words per tile row
+    if (cols == T) {
+        for (int idx = threadIdx.x; idx < rows * WPR; idx += blockDim.x) {
+            const int x = idx / WPR, y0 = (idx % WPR) * E;
+            uint4 v4;
+            TOut *vp = reinterpret_cast<TOut *>(&v4);
+#pragma unroll
+            for (int e = 0; e < E; ++e) vp[e] = val(x, y0 + e);
+            *reinterpret_cast<uint4 *>(out + (ia + x) * ld + ja + y0) = v4;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
+            const int x = idx >> T_SHIFT, y = idx & (T - 1);
+            if (y < cols) out[(ia + x) * ld + ja + y] = val(x, y);
+        }
+    }
+}
+
 // A tile of the launch as classified by warp 0.
 struct DpxMeta {
     int32_t job, I, J;
@@ -811,12 +838,9 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
             if (m.cst) {
                 // Constant tile: written here, nothing staged.
                 if (layout == LAYOUT_DENSE) {
-                    TOut *out = reinterpret_cast<TOut *>(p.dense_out);
-                    const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
-                    for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
-                        const int x = idx >> T_SHIFT, y = idx & (T - 1);
-                        if (y < cols) out[(int64_t)(ia + x) * p.ld + ja + y] = (TOut)m.val;
-                    }
+                    const TOut cv = (TOut)m.val;
+                    store_dense_tile<TOut>(reinterpret_cast<TOut *>(p.dense_out), p.ld, ia, ja, min(T, n + 1 - ia),
+                                           min(T, n + 1 - ja), [&](int, int) { return cv; });
                 } else {
                     const int64_t tile = (layout == LAYOUT_COL) ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
                     uint4 v4;
@@ -940,14 +964,10 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
             if (layout != LAYOUT_DENSE) fence_proxy_async_smem();
             __syncthreads();
             if (layout == LAYOUT_DENSE) {
-                TOut *out = reinterpret_cast<TOut *>(p.dense_out);
-                const int rows = min(T, n + 1 - ia), cols = min(T, n + 1 - ja);
-                for (int idx = threadIdx.x; idx < rows * T; idx += blockDim.x) {
-                    const int x = idx >> T_SHIFT, y = idx & (T - 1);
-                    if (y >= cols) continue;
-                    const int64_t i = ia + x, j = ja + y;
-                    out[i * p.ld + j] = (i > j) ? Sentinel<TOut>::value : Ds[x * PO + y];
-                }
+                store_dense_tile<TOut>(reinterpret_cast<TOut *>(p.dense_out), p.ld, ia, ja, min(T, n + 1 - ia),
+                                       min(T, n + 1 - ja), [&](int x, int y) {
+                                           return ia + x > ja + y ? Sentinel<TOut>::value : Ds[x * PO + y];
+                                       });
                 __syncthreads();                // Ds read before the next tile writes it
             } else if (threadIdx.x == 0) {
                 const int64_t tile = (layout == LAYOUT_COL) ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
@@ -1079,6 +1099,33 @@ __global__ void fill_dense_kernel(V *out, int64_t n, int64_t ld, V lower, V uppe
         if (fill_upper)
             for (int64_t j = i + threadIdx.x; j <= n; j += blockDim.x) out[i * ld + j] = upper;
     }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) fill_lower_kernel(V *out, int64_t n, int64_t ld, V lower) {
+    pdl_wait_and_release();
+    uint4 v4;
+    V *vp = reinterpret_cast<V *>(&v4);
+#pragma unroll
+    for (int k = 0; k < (int)(16 / sizeof(V)); ++k) vp[k] = lower;
+    for (int64_t i = blockIdx.x; i <= n; i += gridDim.x) {
+        // Columns [0, (i / T) T): whole 16-byte words (T elements are 64 or
+        // 128 bytes), starting at a 16-byte aligned row.
+        const int64_t words = ((i >> T_SHIFT) << T_SHIFT) * (int64_t)sizeof(V) / 16;
+        uint4 *row = reinterpret_cast<uint4 *>(out + i * ld);
+        for (int64_t w = threadIdx.x; w < words; w += blockDim.x) row[w] = v4;
+    }
+}
+
+cudaError_t launch_fill_lower(void *out, int dtype, int64_t n, int64_t ld, int lower, int blocks, cudaStream_t st) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, n + 1));
+    if (dtype == DT_I32)
+        return launch_pdl(fill_lower_kernel<int32_t>, dim3(g), dim3(256), 0, st, (int32_t *)out, n, ld,
+                          (int32_t)lower);
+    if (dtype == DT_I16)
+        return launch_pdl(fill_lower_kernel<int16_t>, dim3(g), dim3(256), 0, st, (int16_t *)out, n, ld,
+                          (int16_t)lower);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fill_dense(void *out, int dtype, int64_t n, int64_t ld, int lower, int upper,
