@@ -236,7 +236,7 @@ def test_invalid_arguments(ctx):
 
 
 @pytest.mark.parametrize("host", ["pinned", "pinned_odd_pitch", "pageable", "pinned_i16", "pinned_no_lcs",
-                                  "pinned_3_levels"])
+                                  "pinned_3_levels", "pinned_one_strip", "pinned_empty_a", "pinned_empty_b"])
 def test_solve_host_roundtrip(ctx, host):
     """Pinned 16-byte-pitch DIST is written by the kernels directly (its
     lower triangle while the tree is built, the rest by the root merge); an
@@ -245,7 +245,8 @@ def test_solve_host_roundtrip(ctx, host):
     waits for the side stream's fill.  Every entry starts at 5, so one the
     solve did not write shows."""
     rng = np.random.default_rng(12)
-    m, n = (1100, 900) if host == "pinned_3_levels" else (333, 444)
+    m, n = {"pinned_3_levels": (1100, 900), "pinned_one_strip": (100, 300), "pinned_empty_a": (0, 37),
+            "pinned_empty_b": (41, 0)}.get(host, (333, 444))
     a, b = inputs.random_pair(rng, m, n)
     B.lcs_set_strip_height(ctx, 0)
     ah = torch.from_numpy(a).pin_memory()
@@ -255,7 +256,7 @@ def test_solve_host_roundtrip(ctx, host):
     dh = torch.full((n + 1, ld), 5, dtype=dt)
     if host != "pageable":
         dh = dh.pin_memory()
-    lh = None if host == "pinned_no_lcs" else torch.zeros(m, dtype=torch.uint8).pin_memory()
+    lh = None if host == "pinned_no_lcs" else torch.zeros(max(m, 1), dtype=torch.uint8).pin_memory()
     L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh)
     s_want, _ = oracle.traceback(a, b)
     assert L == len(s_want)
