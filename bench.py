@@ -26,6 +26,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Hardware work queues of this process's CUDA context (read once, when the
+# context is created, so before torch touches the GPU).  Every batch of the
+# serving loop runs on streams of its own; with the default 8 queues, dozens
+# of batches in flight share them and a small batch's kernels wait behind
+# another batch's long sweeps.  The single-pair solve is unaffected.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "GCUPS (m·n/s) per pair"
 UNIT = "GCUPS"
 L2_FLUSH_BYTES = 256 << 20
@@ -46,6 +53,7 @@ def parse_args():
     ap.add_argument("--no-pair16384", action="store_true", help="skip the m = n = 16384 pair measurement")
     ap.add_argument("--plain-pairs", type=int, default=2000)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrivals per second")
     return ap.parse_args()
 
 
@@ -183,7 +191,7 @@ def pairs_length_dp(pairs, sample):
             "cores": cores, "seconds": t, "pairs": len(pairs), "sample": sample}
 
 
-def workload_baselines(batched, serve_seconds, serve_sample=2000):
+def workload_baselines(batched, serve_seconds, serve_rate=2000.0, serve_sample=2000):
     """Host baselines of the batched and serving workloads (the same seeded
     pairs the GPU measurements use)."""
     from paper_2309_09072_gb300 import inputs
@@ -192,7 +200,7 @@ def workload_baselines(batched, serve_seconds, serve_sample=2000):
         out["batched_length_dp"] = pairs_length_dp(inputs.batch_pairs(), "all 20,000 pairs of the batched workload")
     if serve_seconds > 0:
         import oracle
-        _, req = inputs.serving_requests(duration_s=serve_seconds)
+        _, req = inputs.serving_requests(duration_s=serve_seconds, rate=serve_rate)
         req = req[:serve_sample]
         r = pairs_length_dp(req, "the first %d requests of the serving workload" % len(req))
         big = next(((x, y) for x, y in req if len(x) * len(y) >= 16384 * 16384), None)
@@ -432,22 +440,22 @@ def batched_measure(B, torch, plain_pairs, reps=3):
             "batched_over_plain": bv / pv}
 
 
-def serving_measure(B, torch, seconds):
-    """The serving workload (Poisson arrivals at 2,000 pairs/s, 20 letters,
+def serving_measure(B, torch, seconds, rate=2000.0):
+    """The serving workload (Poisson arrivals at `rate` pairs/s, 20 letters,
     lengths log-uniform in [128, 8192], every 50th pair 16384 x 16384, 30%
     correlated) for `seconds` seconds of arrivals through continuous batching
     (serve.py over lcs_batch_submit/poll), strings resident on the device."""
     from paper_2309_09072_gb300 import inputs, serve
-    times, pairs = inputs.serving_requests(duration_s=seconds)
+    times, pairs = inputs.serving_requests(duration_s=seconds, rate=rate)
     dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
     ctx = B.lcs_create(0, 0)
     serve.serve(ctx, dev[:50], times[:50] - times[0])          # warm-up on the first requests
     out = serve.serve(ctx, dev, times)
     B.lcs_destroy(ctx)
     summ = serve.summary(out, [(len(a), len(b)) for a, b in pairs])
-    summ.update({"workload": "serving: Poisson 2,000 pairs/s for %.0f s, 20 letters, lengths log-uniform "
+    summ.update({"workload": "serving: Poisson %s pairs/s for %.0f s, 20 letters, lengths log-uniform "
                              "[128, 8192], every 50th pair 16384 x 16384, 30%% correlated; one LCS per pair"
-                             % seconds,
+                             % (format(int(rate), ","), seconds),
                  "latency": "device completion of the request's batch minus its arrival"})
     return summ
 
@@ -569,10 +577,10 @@ def run_ours(args):
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_measure(B, torch, args.plain_pairs)
     if rank == 0 and args.serve_seconds > 0:
-        line["serving"] = serving_measure(B, torch, args.serve_seconds)
+        line["serving"] = serving_measure(B, torch, args.serve_seconds, args.serve_rate)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, b)
-        line["cpu_baseline"].update(workload_baselines(not args.no_batched, args.serve_seconds))
+        line["cpu_baseline"].update(workload_baselines(not args.no_batched, args.serve_seconds, args.serve_rate))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

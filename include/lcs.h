@@ -327,10 +327,16 @@ lcs_status lcs_solve_host(lcs_ctx *ctx, const uint8_t *a_host, int64_t m,
  * pairs of uneven lengths is this library's extension of it.  A pair whose a
  * has at most 16384 letters is one strip (all its rows fit one bit vector),
  * so its tree has no merge level: the length is the strip's DIST(0, n) and
- * one LCS the strip's leftmost heaviest path, computed a warp per pair in one
- * launch per size class (a up to 2048, 4096, 8192, 16384 rows), the classes
- * side by side.  Taller pairs go through the strip tree of lcs_solve, one
- * after another, inside lcs_batch_submit.
+ * one LCS the strip's leftmost heaviest path.  Pairs of up to 4096 rows run a
+ * warp per pair in one launch per size class (a up to 2048 and up to 4096
+ * rows), the classes side by side; pairs of 4097..16384 rows spread their
+ * vector over several warps and find the LCS from forward and backward
+ * sweeps.  Taller pairs go through the strip tree of lcs_solve, one after
+ * another, inside lcs_batch_submit.  Each batch runs on streams of its own:
+ * a process with many batches in flight should raise the
+ * CUDA_DEVICE_MAX_CONNECTIONS environment variable (32, say) before CUDA is
+ * initialised, or the batches' kernels queue behind one another in the
+ * default 8 hardware queues.
  * ---------------------------------------------------------------------- */
 #define LCS_WANT_STRING 1u
 

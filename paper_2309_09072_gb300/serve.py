@@ -10,6 +10,12 @@ released.  Finished batches are found by non-blocking polls; each request's
 latency is its batch's device completion minus its arrival, both on the
 monotonic clock the library uses.
 
+Each batch in flight has streams of its own, so a process that serves at a
+high rate should raise CUDA_DEVICE_MAX_CONNECTIONS (32, say) before CUDA is
+initialised.  With the default 8 hardware queues the streams of dozens of
+batches share them, and a small batch's kernels wait behind another batch's
+long sweeps.
+
 This module schedules and records only; every computation runs in the
 library's kernels.
 """
