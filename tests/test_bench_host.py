@@ -86,3 +86,18 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(0.5, 1) == 0.5
     assert bench.aggregate_gcups(1, 10, 10, 2, 1.0) == pytest.approx(2e-7)
+
+
+def test_bench_sets_work_queues_without_overriding():
+    """bench.py raises the context's hardware work queues for the serving
+    measurement, unless the caller chose a value."""
+    import subprocess
+    import sys
+    code = "import os, bench; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])"
+    env = dict(os.environ)
+    env.pop("CUDA_DEVICE_MAX_CONNECTIONS", None)
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "32", out.stderr
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "12"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "12", out.stderr
