@@ -101,3 +101,32 @@ def test_bench_sets_work_queues_without_overriding():
     env["CUDA_DEVICE_MAX_CONNECTIONS"] = "12"
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "12", out.stderr
+
+
+def test_roofline_arithmetic():
+    """achieved = algorithmic bytes (or ops) per launch / mean launch time,
+    frac = achieved / peak, for the kernel with the largest device time; the
+    merge's DRAM traffic and DPX pipe figures come from the committed ncu
+    summary while merge.cu matches its recorded hash."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"hbm_gbs": 6697.2}
+    int_peak = {"derived_gops": 40276.0, "measured_gops": 39000.0}
+    prof = {"merge_tile": {"launches": 200, "ms": 20.0, "bytes": 200 * 193.0e6, "ops": 0.0},
+            "strip": {"launches": 50, "ms": 9.0, "bytes": 0.0, "ops": 50 * 3.0e12 * 1e-3}}
+    r = bench.roofline(prof, peaks, "measured", int_peak)
+    assert r["kernel"] == "merge_tile" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["ms_per_launch"] == pytest.approx(0.1)
+    assert r["achieved"] == pytest.approx(193.0e6 / 0.1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6697.2)
+    assert r["share_of_device_time"] == pytest.approx(20.0 / 29.0)
+    assert r["traffic"] == bench.recorded_traffic("paper_2309_09072_gb300/csrc/merge.cu",
+                                                  "merge_tile_dpx_pair4096.md")
+    assert r["traffic"] is not None and "measured_bound" in r
+    # A strip-dominated profile is counted against the derived INT32 peak.
+    prof["strip"]["ms"] = 40.0
+    r = bench.roofline(prof, peaks, "measured", int_peak)
+    assert r["kernel"] == "strip" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(3.0e9 / 0.8e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 40276.0)
+    assert bench.roofline({}, peaks, "measured", int_peak) is None
