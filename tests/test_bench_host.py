@@ -130,3 +130,36 @@ def test_roofline_arithmetic():
     assert r["achieved"] == pytest.approx(3.0e9 / 0.8e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 40276.0)
     assert bench.roofline({}, peaks, "measured", int_peak) is None
+
+
+def test_clock_sampler_summary(monkeypatch):
+    """Median SM clock under load, the maximum, and every throttle reason seen
+    Active during the timed region (a fake nvidia-smi process)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = ("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 1980, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+            "0, 2070, 2070, 1300.2, 0x8, Active, Not Active, Not Active, Not Active\n"
+            "garbage line\n")
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def kill(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return rows, None
+
+    monkeypatch.setattr(bench.subprocess, "Popen", lambda *a, **k: FakeProc())
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    c = bench.ClockSampler(0).stop()
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+    def no_smi(*a, **k):
+        raise OSError("nvidia-smi not found")
+
+    monkeypatch.setattr(bench.subprocess, "Popen", no_smi)
+    assert bench.ClockSampler(0).stop() is None
