@@ -71,11 +71,14 @@ int oracle_dist_row(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
     int32_t *prev = (int32_t *)calloc((size_t)w + 1, sizeof(int32_t));
     int32_t *cur = (int32_t *)calloc((size_t)w + 1, sizeof(int32_t));
     if (!prev || !cur) { free(prev); free(cur); return -1; }
+    /* The heaviest path into vertex (r, c) arrives by the down edge, the
+     * right edge or the diagonal (weight [a_r = b_c]), so each cell is the
+     * maximum of those three terms. */
     for (int64_t r = 1; r <= m; ++r) {
         cur[0] = 0;
         for (int64_t c = 1; c <= w; ++c) {
-            if (a[r - 1] == b[i + c - 1]) cur[c] = prev[c - 1] + 1;
-            else cur[c] = max_i32(prev[c], cur[c - 1]);
+            const int32_t diag = prev[c - 1] + (a[r - 1] == b[i + c - 1] ? 1 : 0);
+            cur[c] = max_i32(max_i32(prev[c], cur[c - 1]), diag);
         }
         int32_t *t = prev; prev = cur; cur = t;
     }
