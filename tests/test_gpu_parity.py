@@ -282,17 +282,14 @@ def test_pair_4096(ctx, variant):
     s, cross, L, D = gpu_solve(ctx, a, b, with_dist=True)
     s_want, v_want = oracle.traceback(a, b)
     assert L == len(s_want) and s == s_want and np.array_equal(cross, v_want)
-    if variant == "iid":
-        assert np.array_equal(D, oracle.dist(a, b))
-    else:
-        rows = np.unique(np.concatenate([[0, 1, 63, 64, 2047, 4095, 4096],
-                                         np.random.default_rng(0).integers(0, 4097, 24)]))
-        assert np.array_equal(D[rows], oracle.dist_rows(a, b, rows))
+    assert np.array_equal(D, oracle.dist(a, b))
 
 
-def test_pair_16384_sampled(ctx):
-    """m = n = 16384, 20 letters Zipf(1.1), int16 DIST: 64 seeded rows plus the
-    tile-boundary rows, element by element; length; LCS."""
+def test_pair_16384_full(ctx):
+    """m = n = 16384, 20 letters Zipf(1.1), int16 DIST: every one of the
+    16385 x 16385 entries against the oracle's per-source DP (about 2.2e12
+    cell updates spread over the host cores, compared in blocks of rows);
+    length; LCS."""
     a, b = inputs.pair_16384()
     n = len(b)
     B.lcs_set_strip_height(ctx, 0)
@@ -302,11 +299,14 @@ def test_pair_16384_sampled(ctx):
     B.lcs_solve(ctx, dev(a), dev(b), dist=d, out_lcs=out, out_len=ln)
     B.lcs_sync(ctx)
     L = int(ln.item())
-    rows = np.unique(np.concatenate([[0, 1, 63, 64, 8191, 16320, 16383, 16384],
-                                     np.random.default_rng(16384).integers(0, n + 1, 64)])).astype(np.int64)
-    got = d[torch.from_numpy(rows).cuda(), : n + 1].cpu().numpy().astype(np.int64)
-    want = oracle.dist_rows(a, b, rows).astype(np.int64)
-    want[want == np.iinfo(np.int32).min] = np.iinfo(np.int16).min
-    assert np.array_equal(got, want)
     s_want, _ = oracle.traceback(a, b)
     assert L == len(s_want) and bytes(out[:L].cpu().numpy()) == s_want
+    got = d[:, : n + 1].cpu().numpy()
+    del d
+    block = 1024
+    for r0 in range(0, n + 1, block):
+        rows = np.arange(r0, min(n + 1, r0 + block), dtype=np.int64)
+        want = oracle.dist_rows(a, b, rows)
+        want[want == np.iinfo(np.int32).min] = np.iinfo(np.int16).min
+        bad = np.argwhere(got[rows].astype(np.int32) != want)
+        assert bad.size == 0, f"first mismatch at (i, j) = ({rows[bad[0][0]]}, {bad[0][1]})"

@@ -2,7 +2,8 @@
 
 Its scratch lives in a static device array inside the library, so it must
 give exactly what lcs_merge gives (same D and same argmax), call after call,
-even though every call reuses the same array.  This file is collected last so
+even though every call reuses the same array; both must equal the oracle's
+brute-force merge (every k, smallest maximiser).  This file is collected last so
 that a run stopping at the first failure has already run everything else; it
 also passes on its own in a fresh process.
 """
@@ -27,13 +28,22 @@ def _operands(seed, n, dtype):
     ld = ((n + 1) * elem + 15) // 16 * 16 // elem
     sentinel = np.iinfo(np.int32).min if dtype == torch.int32 else np.iinfo(np.int16).min
     out = []
+    Uo, Lo = U.astype(np.int32), L.astype(np.int32)
     for M in (U, L):
         M = M.copy()
         M[M < -40000] = sentinel
         t = torch.full((n + 1, ld), 0, dtype=dtype, device="cuda")
         t[:, : n + 1] = torch.from_numpy(M).to(dtype).cuda()
         out.append(t)
-    return out[0], out[1], ld
+    return out[0], out[1], ld, Uo, Lo
+
+
+def _oracle_merge(Uo, Lo, dtype):
+    D, K = oracle.merge(Uo, Lo)
+    D = D.astype(np.int64)
+    if dtype == torch.int16:
+        D[D == np.iinfo(np.int32).min] = np.iinfo(np.int16).min
+    return D, K.astype(np.int64)
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +58,7 @@ def ctx():
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int16])
 def test_static_merge_matches_lcs_merge_twice(ctx, dtype):
     for call, (seed, n) in enumerate([(11, 1024), (12, 333)]):      # two calls in a row
-        U, L, ld = _operands(seed + (dtype == torch.int16), n, dtype)
+        U, L, ld, Uo, Lo = _operands(seed + (dtype == torch.int16), n, dtype)
         d_ref = torch.full_like(U, 9)
         k_ref = torch.full(U.shape, -9, dtype=torch.int32, device="cuda")
         B.lcs_merge(ctx, U, L, d_ref, k_ref)
@@ -58,16 +68,20 @@ def test_static_merge_matches_lcs_merge_twice(ctx, dtype):
         B.lcs_merge_static(U, L, d_st, k_st)
         assert torch.equal(d_st[:, : n + 1], d_ref[:, : n + 1]), (call, n)
         assert torch.equal(k_st[:, : n + 1], k_ref[:, : n + 1]), (call, n)
+        D_want, K_want = _oracle_merge(Uo, Lo, dtype)
+        assert np.array_equal(d_st[:, : n + 1].cpu().numpy().astype(np.int64), D_want), (call, n)
+        assert np.array_equal(k_st[:, : n + 1].cpu().numpy().astype(np.int64), K_want), (call, n)
 
 
 def test_static_merge_without_argmax_and_limit(ctx):
-    U, L, ld = _operands(21, 200, torch.int32)
+    U, L, ld, Uo, Lo = _operands(21, 200, torch.int32)
     d_ref = torch.zeros_like(U)
     B.lcs_merge(ctx, U, L, d_ref)
     B.lcs_sync(ctx)
     d_st = torch.ones_like(U)
     B.lcs_merge_static(U, L, d_st)
     assert torch.equal(d_st[:, :201], d_ref[:, :201])
+    assert np.array_equal(d_st[:, :201].cpu().numpy().astype(np.int64), _oracle_merge(Uo, Lo, torch.int32)[0])
     big = torch.zeros((1026, 1028), dtype=torch.int32, device="cuda")
     with pytest.raises(B.LcsError) as e:
         B.lcs_merge_static(big, big, torch.zeros_like(big))
