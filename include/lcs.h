@@ -136,6 +136,21 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
 enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2 };
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
 
+/* Failure detection, for tests.  Every device-side wait of the merge
+ * kernels (a TMA band copy landing on its mbarrier) is bounded: after
+ * wait_limit_ns of global time (0 restores the default of 2 s) the kernel
+ * records a timeout, gives copies that are only late a second wait of the
+ * same length, skips the tile and returns; lcs_sync (or the synchronous call)
+ * then returns LCS_ETIMEOUT and the context stays usable.  With hold_band
+ * set, the first tile of every later exact-merge launch (lcs_merge, and
+ * lcs_solve / lcs_dist with LCS_MERGE_EXACT) announces its band on its
+ * barrier but copies nothing, so that wait runs out with nothing in flight:
+ * the way to exercise the timeout without faulting or hanging the GPU.
+ * Outputs of such a call are unspecified.  hold_band = 0 and
+ * wait_limit_ns = 0 restore normal operation.  Errors: EINVAL (ctx NULL,
+ * wait_limit_ns < 0). */
+lcs_status lcs_set_fault_injection(lcs_ctx *ctx, int32_t hold_band, int64_t wait_limit_ns);
+
 /* CUDA-graph replay of lcs_solve (1) or plain launches (0, the default).
  * With graphs on, the first lcs_solve with a given set of arguments runs as
  * usual and is then captured (on a private stream) into a graph; later
@@ -221,13 +236,14 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
  * Same arguments and results as lcs_merge, but no context: every scratch
  * byte comes from one static device array of 6 MiB that each GPU loading the
  * library holds until the process exits, which limits n to 1024 (both
- * dtypes; larger n returns EINVAL).  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, with the device
- * current) and caches it, so make that first call before any stream
- * capture.  All calls on a device share the array and it keeps the last
- * call's contents (each call clears what must start at zero); calls that
- * overlap on the GPU race, so serialise them.  Synchronous: returns after
- * the merge has finished on `stream`.
+ * dtypes; larger n returns EINVAL).  The call runs on the current device:
+ * `stream` must belong to it, and so must every pointer.  Each call looks up
+ * that device's copy of the array (cudaGetSymbolAddress, with the device
+ * current), so a context torn down and created again is handled.  All calls
+ * on a device share the array and it keeps the last call's contents (each
+ * call clears what must start at zero); calls that overlap on the GPU race,
+ * so serialise them.  Synchronous: returns after the merge has finished on
+ * `stream`.
  * Errors: EINVAL (n > 1024, bad layout, inputs that are not strip DIST
  * matrices), ECUDA, ETIMEOUT, EOVERFLOW. */
 lcs_status lcs_merge_static(const void *dist_u, const void *dist_l, int64_t n, lcs_dtype dtype, int64_t ld,

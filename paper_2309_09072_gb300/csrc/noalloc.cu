@@ -13,15 +13,16 @@
 //
 // The array is static device memory: every GPU that loads the library holds
 // kStaticScratchBytes of it until the process exits.  In host code its name
-// is only a host-side stand-in, so the device address is looked up once per
-// device with cudaGetSymbolAddress (on the first call on that device, with
-// that device current) and cached.  All calls on a device share the array
-// and it keeps the last call's contents; whatever must start at zero is
+// is only a host-side stand-in, so each call looks the device address up with
+// cudaGetSymbolAddress, with the call's device current.  The lookup is cheap
+// next to the synchronous merge, and it stays right when the device's context
+// is torn down and created again (cudaDeviceReset reloads the module, and the
+// array may then sit at another address).  All calls on a device share the
+// array and it keeps the last call's contents; whatever must start at zero is
 // cleared by each call, and calls that overlap on the GPU race on it.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "lcs.h"
 #include "lcs_common.cuh"
@@ -33,26 +34,16 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)6 << 20;   // 6 MiB per device
 constexpr int64_t kStaticMaxN = 1024;                     // documented in lcs.h
-constexpr int kMaxDevices = 128;
 
 static __device__ __align__(256) unsigned char g_merge_scratch[kStaticScratchBytes];
 
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices];                        // device address per device
-
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Device address of g_merge_scratch on the current device (set up once).
+// Device address of g_merge_scratch in the current device's context.
 lcs_status scratch_address(void **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LCS_ECUDA;
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_merge_scratch) != cudaSuccess || !p) return LCS_ECUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_merge_scratch) != cudaSuccess || !p) return LCS_ECUDA;
+    *out = p;
     return LCS_OK;
 }
 
