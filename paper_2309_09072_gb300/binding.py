@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
             "lcs_set_strip_height": ([vp, i32], st),
             "lcs_set_merge_kernel": ([vp, i32], st),
             "lcs_set_graphs": ([vp, i32], st),
+            "lcs_set_fault_injection": ([vp, i32, i64], st),
             "lcs_autotune": ([vp, vp, i64, vp, i64, i32, vp, i64, vp, i64, vp, ctypes.POINTER(i32),
                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
@@ -249,6 +250,10 @@ LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX = 0, 1, 2
 
 def lcs_set_merge_kernel(ctx, kind: int) -> None:
     _check(ctx, load().lcs_set_merge_kernel(ctx, int(kind)))
+
+
+def lcs_set_fault_injection(ctx, hold_band: bool, wait_limit_ns: int = 0) -> None:
+    _check(ctx, load().lcs_set_fault_injection(ctx, 1 if hold_band else 0, int(wait_limit_ns)))
 
 
 def lcs_set_graphs(ctx, enable: bool) -> None:

@@ -148,6 +148,8 @@ struct lcs_ctx {
     size_t budget = 0;
     int32_t strip_h = 0;
     int32_t merge_kernel = LCS_MERGE_AUTO;
+    uint64_t wait_ns = 0;        // bounded device waits (0: the kernels' default)
+    int32_t hold_band = 0;       // fault injection (lcs_set_fault_injection)
     char *ws = nullptr;          // plan workspace
     size_t ws_bytes = 0;
     char *io = nullptr;          // host-call staging (lcs_solve_host, lcs_merge)
@@ -457,9 +459,9 @@ lcs_status ensure_io(lcs_ctx *ctx, size_t bytes) {
 
 // Strip height when none is set: 256 rows (eight 32-bit words per bit
 // vector).  Halving h doubles the strips but adds a tree level of merges,
-// the dominant cost: at m = n = 4096 a solve takes 1.00 ms at h = 256
-// against 1.24 ms at h = 128 and 1.71 ms at h = 64.  A smaller h set by the
-// caller is doubled while the retained tree would not fit the budget.
+// the dominant cost, so at m = n = 4096 the autotuner's candidates 64, 128
+// and 256 rank in that order, slowest first.  A smaller h set by the caller
+// is doubled while the retained tree would not fit the budget.
 int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
     int h = auto_strip_height(m, n);
     while (h < 256 && m > h) {
@@ -698,6 +700,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             mp.dense_out = g.root ? dist : nullptr;
             mp.dense_K = nullptr;
             mp.const_tiles = 1;
+            mp.wait_ns = ctx->wait_ns; mp.hold_band = ctx->hold_band;
             mp.sigma = (int32_t)sigma0; mp.full = 1;
             LCS_LAUNCHK(ctx, gs, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, gs));
             for (int64_t sg = sigma0 / 2; sg >= 1; sg /= 2) {
@@ -864,6 +867,14 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
     if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
     ctx->merge_kernel = kind;
+    return LCS_OK;
+}
+
+lcs_status lcs_set_fault_injection(lcs_ctx *ctx, int32_t hold_band, int64_t wait_limit_ns) {
+    if (!ctx || wait_limit_ns < 0) return fail(ctx, LCS_EINVAL, "fault injection arguments");
+    ctx->hold_band = hold_band ? 1 : 0;
+    ctx->wait_ns = (uint64_t)wait_limit_ns;
+    ctx->gkey.clear();           // a captured solve holds the old launch parameters
     return LCS_OK;
 }
 
@@ -1095,6 +1106,7 @@ lcs_status lcs_merge(lcs_ctx *ctx, const void *dist_u, const void *dist_l, int64
     mp.n = n; mp.NT = NT; mp.P = P; mp.ld = ld; mp.err = err_word(ctx);
     mp.dense_out = dist_out; mp.dense_K = argmax_out;
     mp.const_tiles = argmax_out ? 0 : 1;      // a constant tile has no argmax to report
+    mp.wait_ns = ctx->wait_ns; mp.hold_band = ctx->hold_band;
     const int64_t sigma0 = coarse_sigma0(std::max<int64_t>(P, 1));
     mp.sigma = (int32_t)sigma0; mp.full = 1;
     LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, dt, st));

@@ -59,6 +59,9 @@ struct MergeParams {
     int32_t const_tiles;   // 1: write tiles whose corner values agree as constants
     int32_t grab;          // DPX launch: tiles taken from `sched` at a time (set by the launcher)
     unsigned int *sched;   // DPX launch: tile counter (zero at launch) for dynamic scheduling, or null
+    uint64_t wait_ns;      // limit of each bounded device wait (0: kWaitLimitNs)
+    int32_t hold_band;     // test only: the first staged tile arms its barrier but copies nothing
+    int32_t pad2;
 };
 
 // K-tiles per band for the main tile launch and the spill launch.

@@ -551,14 +551,18 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
             if (Bi == T && kt1 >= ufirst) bytes += (uint32_t)(kt1 - ufirst + 1) * rowB;
             if (Bj == T) bytes += (uint32_t)(ltop2 - kt0 + 1) * rowB;
             mbar_arrive_expect_tx(bar, bytes);
-            for (int kt = kt0; kt <= kt1; ++kt) {
+            // Fault injection (tests only): the band of the launch's first
+            // tile is announced on the barrier but never copied, so its wait
+            // runs out and the tile reports ERR_TIMEOUT with nothing in flight.
+            const bool held = p.hold_band && blockIdx.x == 0 && blockIdx.y == 0;
+            for (int kt = kt0; kt <= kt1 && !held; ++kt) {
                 TIn *dst = Us + (kt - kt0) * BUF;
                 bulk_g2s(dst, Ug + row_tile(I, kt, NT) * EI, tileB, bar);
                 if (Bi == T && kt >= ufirst) bulk_g2s(dst + T * PI, Ug + row_tile(I + 1, kt, NT) * EI, rowB, bar);
             }
-            for (int kt = kt0; kt <= ltop; ++kt)
+            for (int kt = kt0; kt <= ltop && !held; ++kt)
                 bulk_g2s(Ls + (kt - kt0) * BUF, Lg + col_tile(kt, J) * EI, tileB, bar);
-            if (Bj == T)
+            if (Bj == T && !held)
                 for (int kt = kt0; kt <= ltop2; ++kt)
                     bulk_g2s(Ls + (kt - kt0) * BUF + T * PI, Lg + col_tile(kt, J + 1) * EI, rowB, bar);
         }
@@ -580,9 +584,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(MergeParams p) {
         Ks[Bi * TP1] = kcorner(pb, qa);
         Ks[Bi * TP1 + Bj] = khi;
         // One thread waits for the band (bounded); the others park at the barrier.
-        if (in_smem && !mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+        const uint64_t lim = p.wait_ns ? p.wait_ns : kWaitLimitNs;
+        if (in_smem && !mbar_wait_bounded(bar, 0, lim)) {
             set_error(p.err, ERR_TIMEOUT);
             s_ok = 0;
+            // Copies that are only late still land before the CTA's shared
+            // memory is released (a second bounded wait).
+            mbar_wait_bounded(bar, 0, lim);
         }
     }
     __syncthreads();
@@ -752,6 +760,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     const int knT = n >> T_SHIFT, kn = n & (T - 1);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int lane = threadIdx.x & 31;
+    const uint64_t lim = p.wait_ns ? p.wait_ns : kWaitLimitNs;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -867,9 +876,14 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                     if (!(st_tile == l && st_c0 == c0)) issue(m, c0);   // not prefetched
                     st_tile = -1;
                     s_ok = 1;
-                    if (!mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+                    if (!mbar_wait_bounded(bar, phase, lim)) {
                         set_error(p.err, ERR_TIMEOUT);
                         s_ok = 0;
+                        // Before the early return: copies that are only late
+                        // land (a second bounded wait) and the previous
+                        // tile's bulk store has read its shared memory.
+                        mbar_wait_bounded(bar, phase, lim);
+                        bulk_wait_all0();
                     }
                     phase ^= 1u;
                 }
@@ -980,7 +994,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     if (threadIdx.x == 0) {
         // A copy still in flight (prefetched past an error) lands before the
         // CTA's shared memory goes away.
-        if (st_tile >= 0 && !mbar_wait_bounded(bar, phase, kWaitLimitNs)) set_error(p.err, ERR_TIMEOUT);
+        if (st_tile >= 0 && !mbar_wait_bounded(bar, phase, lim)) set_error(p.err, ERR_TIMEOUT);
         bulk_wait_all0();
     }
 }
