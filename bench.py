@@ -51,8 +51,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pair16384", action="store_true", help="skip the m = n = 16384 pair measurement")
-    ap.add_argument("--plain-pairs", type=int, default=2000)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--plain-pairs", type=int, default=20000,
+                    help="pairs of the batched workload run one lcs_batch_submit each (the plain form)")
+    ap.add_argument("--tree-pairs", type=int, default=2000,
+                    help="pairs of the batched workload run through lcs_solve one by one (tree path)")
+    ap.add_argument("--pair16384-steps", type=int, default=10)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrivals per second")
     return ap.parse_args()
 
@@ -130,20 +134,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(a, b, stride, nthreads=0):
-    """Time the oracle on every stride-th DIST row plus the full traceback and
-    extrapolate to the whole step (all n+1 rows).  Returns (seconds, threads)."""
-    import numpy as np
+def oracle_step(a, b, nthreads=0):
+    """Time one complete step of the oracle: every one of the n+1 DIST rows
+    (the per-source DP, sources spread over the host threads) plus the
+    leftmost traceback.  Nothing is extrapolated.  Returns (seconds, threads)."""
     import oracle
-    n = len(b)
-    rows = np.arange(0, n + 1, stride, dtype=np.int64)
     t0 = time.perf_counter()
-    oracle.dist_rows(a, b, rows, nthreads)
-    t1 = time.perf_counter()
+    oracle.dist(a, b, nthreads)
     oracle.traceback(a, b)
-    t2 = time.perf_counter()
-    threads = nthreads or os.cpu_count() or 1
-    return (t1 - t0) * (n + 1) / len(rows) + (t2 - t1), threads
+    t = time.perf_counter() - t0
+    return t, nthreads or os.cpu_count() or 1
 
 
 def length_dp_baseline(a, b):
@@ -212,13 +212,23 @@ def workload_baselines(batched, serve_seconds, serve_rate=2000.0, serve_sample=2
     return out
 
 
-def cpu_baseline(a, b, stride=4):
+def cpu_baseline(a, b):
     m, n = len(a), len(b)
-    t, threads = oracle_sample(a, b, stride)
+    t, threads = oracle_step(a, b)
     return {"value": m * n / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "oracle per-source DIST on every %dth of the %d rows (all host threads), "
-                      "extrapolated to all rows, plus the full O(mn) leftmost traceback" % (stride, n + 1),
+            "seconds": t,
+            "sample": "one complete step, timed: the oracle's per-source DIST for all %d rows (all host "
+                      "threads) plus the full O(mn) leftmost traceback" % (n + 1),
+            "method_rate": method_rate(m, n, t),
             "length_dp": length_dp_baseline(a, b)}
+
+
+def method_rate(m, n, seconds):
+    """The method's own work rate: DIST from every source, m (n+1) n / 2 cell
+    updates per pair (each of the n+1 sources sweeps its remaining columns
+    over all m rows), per second."""
+    return {"value": m * n * (n + 1) / 2 / seconds, "unit": "cell updates/s",
+            "per_pair": m * n * (n + 1) / 2}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -228,13 +238,12 @@ def run_reference(args):
         return 0
     a, b = workload(args.variant, 0)
     m, n = len(a), len(b)
-    stride = 32
     for _ in range(args.warmup):
-        oracle_sample(a, b, stride)
+        oracle_step(a, b)
     total = 0.0
     threads = 1
     for _ in range(args.steps):
-        t, threads = oracle_sample(a, b, stride)
+        t, threads = oracle_step(a, b)
         total += t
     ms = total / args.steps * 1e3
     value = m * n * args.steps / total / 1e9
@@ -242,9 +251,10 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_dict(args.variant, m, n), "impl": "reference",
+            "method_rate": method_rate(m, n, total / args.steps),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "per step: oracle DIST on every %dth row (extrapolated to all rows) + "
-                                       "full traceback" % stride},
+                             "sample": "every step complete and timed: the oracle's per-source DIST for all "
+                                       "%d rows (all host threads) + the full leftmost traceback" % (n + 1)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -315,7 +325,7 @@ def roofline(profile, peaks, peaks_src, int_peak):
             "share_of_device_time": share, "ms_per_launch": per_launch_ms, "launches": p["launches"], **out}
 
 
-def pair16384_measure(B, torch, peaks, peaks_src, steps=3):
+def pair16384_measure(B, torch, peaks, peaks_src, steps=10):
     """The m = n = 16384 pair (20 letters, Zipf(1.1)): int16 DIST of the whole
     grid + length + LCS, autotuned, CUDA-graph replay, timed with CUDA events
     on the launching stream (its 0.5 GB output and ~10 GB of merge operands
@@ -351,6 +361,24 @@ def pair16384_measure(B, torch, peaks, peaks_src, steps=3):
         profile = B.lcs_get_profile(ctx)
         B.lcs_set_profiling(ctx, False)
         stats = B.lcs_get_stats(ctx)
+        L = int(ln.item())
+        # End to end through lcs_solve_host: a and b from pinned host memory,
+        # the 0.5 GB int16 DIST, the LCS and the length back every step.
+        del dist
+        ah = torch.from_numpy(a.copy()).pin_memory()
+        bh = torch.from_numpy(b.copy()).pin_memory()
+        dh = torch.empty((n + 1, ld), dtype=torch.int16).pin_memory()
+        lh = torch.empty(min(m, n), dtype=torch.uint8).pin_memory()
+        B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh, dtype=B.LCS_I16, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            Lh = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh, dtype=B.LCS_I16, stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / steps
+        e2e = {"value": m * n / e2e_s / 1e9, "unit": "GCUPS", "ms_per_step": e2e_s * 1e3, "steps": steps,
+               "h2d_bytes_per_step": m + n, "d2h_bytes_per_step": (n + 1) * (n + 1) * 2 + Lh + 16,
+               "api": "lcs_solve_host (pinned host buffers, int16 DIST)"}
         mt = profile.get("merge_tile")
         merge = None
         if mt:
@@ -362,19 +390,23 @@ def pair16384_measure(B, torch, peaks, peaks_src, steps=3):
                      "launches": mt["launches"]}
         return {"workload": "single pair m=n=16384, 20 letters Zipf(1.1): int16 DIST of the whole grid + LCS "
                             "length + leftmost-argmax LCS", "value": m * n / (ms * 1e-3) / 1e9, "unit": "GCUPS",
-                "ms_per_step": ms, "steps": steps, "strip_height": stats["strip_height"],
+                "ms_per_step": ms, "steps": steps, "method_rate": method_rate(m, n, ms * 1e-3), "e2e": e2e,
+                "strip_height": stats["strip_height"],
                 "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
-                "lcs_length": int(ln.item()), "peak_workspace_bytes": stats["peak_workspace_bytes"],
+                "lcs_length": L, "peak_workspace_bytes": stats["peak_workspace_bytes"],
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
                 "merge_roofline": merge}
     finally:
         B.lcs_destroy(ctx)
 
 
-def batched_measure(B, torch, plain_pairs, reps=3):
-    """The batched form (lcs_batch_submit on the 20,000-pair workload, one LCS
-    per pair) against the plain per-pair form (lcs_solve pair by pair on the
-    first `plain_pairs` pairs), both through the library's C entry points on
+def batched_measure(B, torch, plain_pairs, tree_pairs, reps=3):
+    """The batched form (one lcs_batch_submit of the 20,000-pair workload,
+    one LCS per pair) against the plain per-pair form of the same
+    computation: the same pairs, one lcs_batch_submit + lcs_batch_poll per
+    pair, one after another.  Separately labelled: lcs_solve pair by pair
+    (the strip tree with every source's DIST, a different algorithm) on the
+    first `tree_pairs` pairs.  All through the library's C entry points on
     strings already on the device."""
     import ctypes
     import numpy as np
@@ -411,11 +443,28 @@ def batched_measure(B, torch, plain_pairs, reps=3):
     bad = sum(1 for k in range(len(pairs)) if res[k].status != B.LCS_OK)
     cells = sum(m * n for m, n in sizes)
     batch_s = sorted(times)[len(times) // 2]
-    # Plain per-pair form.
+    # Plain per-pair form: the same kernels, one pair per submission.
     k_plain = min(plain_pairs, len(pairs))
+    one = (B.lcs_result * 1)()
+
+    def one_pair(k):
+        B._check(ctx, lib.lcs_batch_submit(ctx, ctypes.byref(arr[k]), 1, ctypes.byref(ticket)))
+        B._check(ctx, lib.lcs_batch_poll(ctx, ticket.value, one, 1, ctypes.byref(done), -1))
+        B._check(ctx, lib.lcs_batch_release(ctx, ticket.value))
+        return one[0].status
+
+    for k in range(20):
+        one_pair(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_bad = sum(1 for k in range(k_plain) if one_pair(k) != B.LCS_OK)
+    plain_s = time.perf_counter() - t0
+    plain_cells = sum(m * n for m, n in sizes[:k_plain])
+    # The tree path per pair (lcs_solve).
+    k_tree = min(tree_pairs, len(pairs))
     views = []
     off = 0
-    for m, n in sizes[:k_plain]:
+    for m, n in sizes[:k_tree]:
         views.append((dbuf[off:off + m], dbuf[off + m:off + m + n]))
         off += m + n
     out = torch.empty(2048, dtype=torch.uint8, device="cuda")
@@ -427,17 +476,24 @@ def batched_measure(B, torch, plain_pairs, reps=3):
     for a, b in views:
         B.lcs_solve(ctx, a, b, out_lcs=out[:max(1, min(a.numel(), b.numel()))], out_len=ln)
     B.lcs_sync(ctx)
-    plain_s = time.perf_counter() - t0
-    plain_cells = sum(m * n for m, n in sizes[:k_plain])
+    tree_s = time.perf_counter() - t0
+    tree_cells = sum(m * n for m, n in sizes[:k_tree])
     B.lcs_destroy(ctx)
-    bv, pv = cells / batch_s / 1e9, plain_cells / plain_s / 1e9
+    bv, pv, tv = cells / batch_s / 1e9, plain_cells / plain_s / 1e9, tree_cells / tree_s / 1e9
     return {"workload": "20,000 pairs, m and n log-uniform in [32, 2048], ACGT i.i.d., one LCS per pair",
             "value": bv, "unit": UNIT, "ms_per_batch": batch_s * 1e3, "pairs_failed": bad,
             "api": "lcs_batch_submit + lcs_batch_poll (strings resident on the device; host wall time of submit "
                    "to completion, median of %d)" % reps,
-            "plain_value": pv, "plain_api": "lcs_solve per pair (LCS string + length)",
-            "plain_sample": "first %d pairs of the same workload" % k_plain,
-            "batched_over_plain": bv / pv}
+            "plain_value": pv,
+            "plain_api": "the same computation one pair at a time: lcs_batch_submit of one pair, "
+                         "lcs_batch_poll until done, lcs_batch_release, pair after pair",
+            "plain_sample": "%d pairs of the same workload" % k_plain, "plain_pairs_failed": plain_bad,
+            "batched_over_plain": bv / pv,
+            "tree_path_per_pair": {"value": tv, "unit": UNIT, "sample": "first %d pairs" % k_tree,
+                                   "api": "lcs_solve per pair: strip tree with DIST from every source, "
+                                          "merges and traceback (a different algorithm from the batch's "
+                                          "one-strip sweep from source 0)",
+                                   "batched_over_tree_path": bv / tv}}
 
 
 def serving_measure(B, torch, seconds, rate=2000.0):
@@ -456,7 +512,9 @@ def serving_measure(B, torch, seconds, rate=2000.0):
     summ.update({"workload": "serving: Poisson %s pairs/s for %.0f s, 20 letters, lengths log-uniform "
                              "[128, 8192], every 50th pair 16384 x 16384, 30%% correlated; one LCS per pair"
                              % (format(int(rate), ","), seconds),
-                 "latency": "device completion of the request's batch minus its arrival"})
+                 "latency": "p50_ms/p99_ms/max_ms: device completion of the request's batch minus its "
+                            "arrival; host_*: the loop's receipt of the result (after the poll and the "
+                            "string copy to the host) minus its arrival"})
     return summ
 
 
@@ -566,6 +624,7 @@ def run_ours(args):
                        "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
                        "chosen_by": "lcs_autotune" if args.strip_height == 0 else "--strip-height"},
             "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
+            "method_rate": method_rate(m, n, total_ms * 1e-3 / args.steps / world),
             "roofline": roofline(profile, peaks, peaks_src, int_peak),
             "clocks": clock_info,
             "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
@@ -573,9 +632,9 @@ def run_ours(args):
             "lcs_length": L, "workspace_bytes": stats["peak_workspace_bytes"]}
     B.lcs_destroy(ctx)
     if rank == 0 and not args.no_pair16384:
-        line["pair_16384"] = pair16384_measure(B, torch, peaks, peaks_src)
+        line["pair_16384"] = pair16384_measure(B, torch, peaks, peaks_src, args.pair16384_steps)
     if rank == 0 and not args.no_batched:
-        line["batched"] = batched_measure(B, torch, args.plain_pairs)
+        line["batched"] = batched_measure(B, torch, args.plain_pairs, args.tree_pairs)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = serving_measure(B, torch, args.serve_seconds, args.serve_rate)
     if rank == 0 and not args.no_cpu_baseline:

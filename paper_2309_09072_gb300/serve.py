@@ -6,9 +6,10 @@ submits the requests that have arrived and are not yet admitted as one batch
 admitted while others are still on the GPU overlaps with them.  A batch that
 does not fit the context's memory budget next to the batches in flight is
 refused (EAGAIN) and its requests wait until finished batches have been
-released.  Finished batches are found by non-blocking polls; each request's
-latency is its batch's device completion minus its arrival, both on the
-monotonic clock the library uses.
+released.  Finished batches are found by non-blocking polls.  Each request
+gets two latencies, both from its arrival on the monotonic clock the library
+uses: to its batch's device completion, and to the loop's receipt of the
+result on the host (after the poll and the copy of the batch's strings).
 
 Each batch in flight has streams of its own, so a process that serves at a
 high rate should raise CUDA_DEVICE_MAX_CONNECTIONS (32, say) before CUDA is
@@ -33,7 +34,8 @@ from . import binding as B
 class ServeResult:
     def __init__(self, count):
         self.length = np.full(count, -1, dtype=np.int64)
-        self.latency_s = np.full(count, np.nan)
+        self.latency_s = np.full(count, np.nan)        # device completion - arrival
+        self.host_latency_s = np.full(count, np.nan)   # receipt on the host - arrival
         self.strings = [b""] * count
         self.status = np.zeros(count, dtype=np.int64)
         self.batches = 0
@@ -88,12 +90,14 @@ def serve(ctx, pairs, arrivals, want_strings=True, max_batch=4096, tick_s=0.0005
         for tk in finished:
             idx, res = inflight.pop(tk)
             strings = B.lcs_batch_strings(ctx, tk) if want_strings else b""
+            t_host = time.monotonic()
             B.lcs_batch_release(ctx, tk)
             for k, q in enumerate(idx):
                 r = res[k]
                 out.length[q] = r.len
                 out.status[q] = r.status
                 out.latency_s[q] = r.t_done - (t0 + arrivals[q])
+                out.host_latency_s[q] = t_host - (t0 + arrivals[q])
                 if want_strings and r.string_offset >= 0:
                     out.strings[q] = strings[r.string_offset: r.string_offset + r.len]
             done += len(idx)
@@ -110,9 +114,12 @@ def serve(ctx, pairs, arrivals, want_strings=True, max_batch=4096, tick_s=0.0005
 def summary(out: ServeResult, pairs_mn):
     """p50/p99 latency (ms), throughput (GCUPS over the wall time), counts."""
     lat = out.latency_s[np.isfinite(out.latency_s)] * 1e3
+    hl = out.host_latency_s[np.isfinite(out.host_latency_s)] * 1e3
     cells = float(sum(m * n for m, n in pairs_mn))
-    return {"requests": len(out.length), "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-            "max_ms": float(lat.max()) if len(lat) else None, "gcups": cells / out.wall_s / 1e9,
+    pct = lambda x, q: float(np.percentile(x, q)) if len(x) else None
+    return {"requests": len(out.length), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "max_ms": float(lat.max()) if len(lat) else None,
+            "host_p50_ms": pct(hl, 50), "host_p99_ms": pct(hl, 99),
+            "host_max_ms": float(hl.max()) if len(hl) else None, "gcups": cells / out.wall_s / 1e9,
             "wall_s": out.wall_s, "batches": out.batches, "refused_submits": out.refused,
             "failed": int((out.status != 0).sum())}

@@ -113,6 +113,9 @@ def test_every_request_completes_with_its_own_result(fake):
     assert out.batches >= 1 and out.refused == 0 and not fake.tickets      # all released
     s = serve.summary(out, [(a.numel(), b.numel()) for a, b in pairs])
     assert s["requests"] == 300 and s["failed"] == 0 and s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+    assert s["host_p50_ms"] <= s["host_p99_ms"] <= s["host_max_ms"]
+    # The host receives a result only after the batch has completed.
+    assert np.all(out.host_latency_s >= out.latency_s - 1e-6)
 
 
 def test_refused_batches_wait_for_memory_and_still_complete(fake):
