@@ -121,19 +121,25 @@ const char *lcs_last_error(lcs_ctx *ctx);
 lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
 
 /* Kernel that computes the tree's merge tiles (Sec. II-B-3: every entry of
- * D(i, j) = max_k U(i, k) + L(k, j)).  Both give the same D, so the choice
+ * D(i, j) = max_k U(i, k) + L(k, j)).  All give the same D, so the choice
  * changes speed only.
- *   LCS_MERGE_AUTO   LCS_MERGE_DPX when every merge operand of the tree
- *                    fits int16 values <= 16383 (strips of <= 16383 rows
- *                    below the root), else LCS_MERGE_EXACT.
- *   LCS_MERGE_EXACT  Monge-windowed refinement of each 64 x 64 tile from
- *                    its corner maximisers, with the exact leftmost argmax.
- *   LCS_MERGE_DPX    (max,+) product of each tile over the band between its
- *                    corner maximisers on DPX instructions (D only); where
- *                    the operands do not fit int16, EXACT is used.
+ *   LCS_MERGE_AUTO      LCS_MERGE_DPX when every merge operand of the tree
+ *                       fits int16 values <= 16383 (strips of <= 16383 rows
+ *                       below the root), else LCS_MERGE_EXACT.
+ *   LCS_MERGE_EXACT     Monge-windowed refinement of each 64 x 64 tile from
+ *                       its corner maximisers, with the exact leftmost argmax.
+ *   LCS_MERGE_DPX       (max,+) product of each 32 x 32 quadrant over the
+ *                       band [x, y] between the largest maximiser x of its
+ *                       top-left corner and the smallest y of its
+ *                       bottom-right corner, on DPX instructions (D only),
+ *                       one warp per quadrant; where the operands do not fit
+ *                       int16, EXACT is used.
+ *   LCS_MERGE_DPX_TILE  the same product per 64 x 64 tile over the band of
+ *                       its corners' smallest maximisers (the earlier DPX
+ *                       kernel, kept for comparison).
  * Applies to lcs_solve* and lcs_dist* on this ctx; lcs_merge, which returns
  * the argmax, always refines exactly.  Errors: EINVAL. */
-enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2 };
+enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2, LCS_MERGE_DPX_TILE = 3 };
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
 
 /* Failure detection, for tests.  Every device-side wait of the merge

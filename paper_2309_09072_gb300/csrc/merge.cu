@@ -36,6 +36,10 @@ namespace lcsg {
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ int64_t grid_vertex(int64_t p, int64_t n) { return min(p * T, n); }
+// Vertex of coarse-grid index p at spacing 2^gshift (gshift 0: T).
+__device__ __forceinline__ int64_t grid_vertex_s(int64_t p, int64_t n, int gshift) {
+    return min(p << (gshift ? gshift : T_SHIFT), n);
+}
 
 // Warp-wide (value, k) reduction: largest value, smallest k among equals.
 __device__ __forceinline__ void warp_argmax(int &v, int &k) {
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
         if (!p.full && !newp && !newq) continue;
         const MergeJob jb = p.jobs[job];
         int32_t *kg = jb.kgrid;
-        const int gi = (int)grid_vertex(xp, n), gj = (int)grid_vertex(xq, n);
+        const int gi = (int)grid_vertex_s(xp, n, p.gshift), gj = (int)grid_vertex_s(xq, n, p.gshift);
         int lo = gi, hi = gj;
         if (!p.full) {
             const int64_t td = newp ? t - 1 : t, tu = newp ? t + 1 : t;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(256) coarse_full_kernel(MergeParams p) {
     const MergeJob jb = p.jobs[job];
     const TIn *U = reinterpret_cast<const TIn *>(jb.U);
     const TIn *L = reinterpret_cast<const TIn *>(jb.L);
-    const int gi = (int)grid_vertex(xp, n), gj = (int)grid_vertex(xq, n);
+    const int gi = (int)grid_vertex_s(xp, n, p.gshift), gj = (int)grid_vertex_s(xq, n, p.gshift);
     int best = INT32_MIN, bk = INT32_MAX;
 #pragma unroll 4
     for (int k = gi + (int)threadIdx.x; k <= gj; k += blockDim.x) {

@@ -1,0 +1,385 @@
+// quad.cu -- the tree's (max,+) merge on DPX instructions, by 32 x 32 quadrants.
+//
+//     D(i, j) = max_{i <= k <= j} U(i, k) + L(k, j)
+//
+// (Sec. II-A's split of a heaviest path at the boundary row between the two
+// halves; Sec. II-B-1's combination formula in its DIST form.)  Only D is
+// produced: the traceback recomputes the maximiser at the one (i, j) of each
+// node that the path uses.
+//
+// The band of a quadrant.  U and L are DIST matrices, hence Monge, and for
+// two points a <= c (both coordinates) with maximisers k_a of a and k_c of c,
+// k_a > k_c implies that k_a also maximises c and k_c also maximises a (add
+// the two Monge inequalities of U and L; the sum can only be an equality).
+// Take the quadrant's top-left corner a = (ia, ja) and bottom-right corner
+// b = (ia + 32, ja + 32), y = K(b) the smallest maximiser of b, and x the
+// largest maximiser of a that is <= y (x >= K(a), since K is monotone).
+// For every (i, j) of the quadrant a <= (i, j) <= b, so a maximiser k of
+// (i, j) below x can be replaced by x and one above y by y: the band [x, y]
+// holds a maximiser of every entry.  Against the band [K(a), K(b)] of the
+// smallest maximisers this drops the ties at a, and against a 64 x 64 tile's
+// band it drops about two thirds of the (max,+) terms on the tree merges of
+// the 4096 and 16384 pairs (measured on the oracle's merges).
+//
+// Work layout.  Every warp is on its own: it takes quadrants from a launch-
+// wide counter, classifies each (corner values from the coarse grid at
+// spacing 32, x by a ballot over U(ia, k) + L(k, ja) = D(a) read from L2),
+// writes constant quadrants straight away, and streams the others' bands
+// through two shared-memory slots of one 32-wide k-chunk each (U rows
+// i = ia..ia+31 and L columns j = ja..ja+31, cp.async 8-byte pieces): the
+// next chunk -- of this quadrant or the next -- lands while the current one
+// is multiplied.  A lane owns 8 x 4 outputs (rows ty + 4a, columns tx + 8b),
+// loads 12 operand words per 4 k and issues 64 __viaddmax_s16x2 (max(a + b,
+// c) on two int16 lanes, the pair taken along k).  Masked entries (k < i in
+// U, k > j in L, k > n) hold -16384; every DIST value is at most 16383, so a
+// masked sum stays negative and never wraps.  The quadrant leaves through
+// the slot it was computed from: rows of 8-byte stores into the tile-packed
+// node, or 16-byte stores into the caller's dense matrix.
+//
+// There is no spin-wait: cp.async groups complete by themselves.
+#include <algorithm>
+#include <cstdint>
+
+#include "lcs_common.cuh"
+#include "lcs_kernels.h"
+
+namespace lcsg {
+namespace {
+
+constexpr int Q = 32;                       // quadrant edge
+constexpr int kQuadWarps = 4;               // warps per CTA, each independent
+constexpr int kQuadThreads = 32 * kQuadWarps;
+constexpr int KC = 32;                      // k per staged chunk
+constexpr int SP = KC + 4;                  // slot row pitch (elements): 72 bytes
+constexpr int kSlotElems = 2 * Q * SP;      // U rows then L rows
+constexpr int kSlotBytes = kSlotElems * 2;  // 4608
+constexpr int kWarpBytes = 2 * kSlotBytes;
+constexpr int16_t kNeg = -16384;
+
+__device__ __forceinline__ int64_t gv(int64_t p, int64_t n) { return min(p << 5, n); }
+
+struct QMeta {
+    int job = 0, ia = 0, ja = 0;
+    int x = 0, y = -1;      // band; y < x: nothing staged
+    int valid = 0;
+};
+
+template <typename TOut>
+__global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p) {
+    pdl_wait_and_release();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int16_t *slots = reinterpret_cast<int16_t *>(smem + warp * kWarpBytes);
+    const int n = (int)p.n;
+    const int64_t NT = p.NT, P = p.P;
+    const int64_t NQ = (n + Q) / Q;                         // quadrant rows: ceil((n+1) / 32)
+    const int64_t per_job = NQ * (NQ + 1) / 2, total = per_job * p.njobs;
+    const int tx = lane & 7, ty = lane >> 3;
+
+    // Destination of output row r (0..31) of a quadrant in a tile-packed
+    // node: row layout (i-major tiles) or column layout (tiles stored
+    // transposed, so a quadrant "row" is a column j).
+    auto packed_row = [&](const MergeJob &jb, int ia, int ja, int r) -> TOut * {
+        TOut *D = reinterpret_cast<TOut *>(jb.D);
+        const int I = ia >> T_SHIFT, J = ja >> T_SHIFT;
+        if (jb.d_layout == LAYOUT_COL)
+            return D + col_tile(I, J) * Fmt<TOut>::ELEMS + ((ja & (T - 1)) + r) * Fmt<TOut>::P + (ia & (T - 1));
+        return D + row_tile(I, J, NT) * Fmt<TOut>::ELEMS + ((ia & (T - 1)) + r) * Fmt<TOut>::P + (ja & (T - 1));
+    };
+    // Entry (x, y) of the quadrant at (ia, ja) = val(x, y), stored by the
+    // whole warp: into the caller's dense matrix (rows of 16-byte stores when
+    // all 32 columns exist; the sentinel below the diagonal; nothing past n),
+    // or into a tile-packed node (8-byte pieces of int16 rows).
+    auto store = [&](const MergeJob &jb, int ia, int ja, auto val) {
+        const int rows = min(Q, n + 1 - ia), cols = min(Q, n + 1 - ja);
+        if (jb.d_layout == LAYOUT_DENSE) {
+            TOut *out = reinterpret_cast<TOut *>(p.dense_out);
+            constexpr int E = 16 / (int)sizeof(TOut), PR = Q / E;   // elements per piece, pieces per row
+            if (cols == Q) {
+                for (int c = lane; c < rows * PR; c += 32) {
+                    const int x = c / PR, y0 = (c % PR) * E;
+                    uint4 v4;
+                    TOut *vp = reinterpret_cast<TOut *>(&v4);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        vp[e] = ia + x > ja + y0 + e ? Sentinel<TOut>::value : (TOut)val(x, y0 + e);
+                    *reinterpret_cast<uint4 *>(out + (int64_t)(ia + x) * p.ld + ja + y0) = v4;
+                }
+            } else {
+                for (int c = lane; c < rows * Q; c += 32) {
+                    const int x = c >> 5, y = c & 31;
+                    if (y < cols)
+                        out[(int64_t)(ia + x) * p.ld + ja + y] =
+                            ia + x > ja + y ? Sentinel<TOut>::value : (TOut)val(x, y);
+                }
+            }
+        } else if (sizeof(TOut) == 2) {
+            const bool col = jb.d_layout == LAYOUT_COL;
+            for (int c = lane; c < Q * 8; c += 32) {
+                const int r = c >> 3, y0 = (c & 7) * 4;
+                uint2 v2;
+                TOut *vp = reinterpret_cast<TOut *>(&v2);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) vp[e] = (TOut)(col ? val(y0 + e, r) : val(r, y0 + e));
+                *reinterpret_cast<uint2 *>(packed_row(jb, ia, ja, r) + y0) = v2;
+            }
+        } else {
+            const bool col = jb.d_layout == LAYOUT_COL;
+            for (int c = lane; c < Q * Q; c += 32) {
+                const int r = c >> 5, y = c & 31;
+                packed_row(jb, ia, ja, r)[y] = (TOut)(col ? val(y, r) : val(r, y));
+            }
+        }
+    };
+    auto write_const = [&](const MergeJob &jb, int ia, int ja, int v) {
+        store(jb, ia, ja, [&](int, int) { return v; });
+    };
+    // The accumulators (the pair's two halves maximised) through the slot.
+    auto write_quadrant = [&](const MergeJob &jb, int ia, int ja, uint32_t (&acc)[8][4], int16_t *sl) {
+        TOut *st = reinterpret_cast<TOut *>(sl);
+        constexpr int SPO = Q + 4;           // staged row pitch: 32 x 36 int32 fill the 4608-byte slot
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int x = ty + 4 * a, y = tx + 8 * b;
+                const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+                st[x * SPO + y] = (TOut)v;
+            }
+        __syncwarp();
+        store(jb, ia, ja, [&](int x, int y) { return (int)st[x * SPO + y]; });
+    };
+
+    // Quadrants come from the launch's counter, p.grab at a time.
+    int64_t q_next = 0, q_end = 0;
+    bool drained = false;
+    auto next_index = [&]() -> int64_t {
+        if (q_next >= q_end && !drained) {
+            unsigned g = 0;
+            if (lane == 0) g = atomicAdd(p.sched, (unsigned)p.grab);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            q_next = g;
+            q_end = min((int64_t)g + (int64_t)p.grab, total);
+            drained = q_next >= total;
+        }
+        return q_next < q_end ? q_next++ : -1;
+    };
+
+    // Writes a constant quadrant, or classifies a staged one.  Returns false
+    // for a constant (or empty) quadrant.
+    auto classify = [&](int64_t g, QMeta &m) -> bool {
+        m.valid = 1;
+        m.job = (int)(g / per_job);
+        const int64_t t = g - (int64_t)m.job * per_job;
+        int64_t lo = 0, hi = NQ - 1;                      // quadrant row: largest r with start(r) <= t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (mid * NQ - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
+        }
+        const int I2 = (int)lo, J2 = (int)(lo + (t - (lo * NQ - lo * (lo - 1) / 2)));
+        m.ia = I2 * Q;
+        m.ja = J2 * Q;
+        const MergeJob jb = p.jobs[m.job];
+        // The caller's dense matrix gets the sentinel below the diagonal:
+        // the fill kernels cover everything left of the diagonal 64 x 64
+        // tiles, and the lower-left quadrant of a diagonal tile (no quadrant
+        // of the enumeration) is written with the tile's odd diagonal one.
+        if (jb.d_layout == LAYOUT_DENSE && I2 == J2 && (I2 & 1))
+            store(jb, m.ia, m.ja - Q, [](int, int) { return 0; });   // every entry has i > j
+        const int64_t pa = I2, pb = min((int64_t)I2 + 1, P), qa = J2, qb = min((int64_t)J2 + 1, P);
+        const int ylim = min(m.ja + Q - 1, n);
+        int y = jb.kgrid[pb * (P + 1) + qb];
+        const int va = jb.vgrid[pa * (P + 1) + qa];
+        if (I2 < J2) {
+            // D is nonincreasing in i and nondecreasing in j: the quadrant's
+            // smallest value is at (ib, ja), its largest at (ia, jb).
+            const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
+            if (vmin == vmax) {
+                write_const(jb, m.ia, m.ja, vmax);
+                return false;
+            }
+        }
+        const bool y_ok = y >= m.ia && y <= (int)gv(qb, n);
+        if (!y_ok) {
+            if (lane == 0) set_error(p.err, ERR_BOUNDS);
+            y = ylim;
+        }
+        y = min(y, ylim);
+        // x: the largest k <= y with U(ia, k) + L(k, ja) = D(a), scanning
+        // 32 k at a time downward (k <= ja, the entries of a).
+        int x = -1;
+        if (m.ia == m.ja) {
+            x = m.ia;                                    // a is on the diagonal: k = ia only
+        } else if (y_ok) {
+            const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
+            const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
+            for (int top = min(y, m.ja); top >= m.ia && x < 0; top -= 32) {
+                const int k = top - lane;
+                bool hit = false;
+                if (k >= m.ia) {
+                    const int f = (int)U[row_elem<int16_t>(m.ia, k, NT)] + (int)L[col_elem<int16_t>(k, m.ja)];
+                    hit = f == va;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal) x = top - (__ffs(bal) - 1);
+            }
+        }
+        if (x < 0) {                                     // not a DIST's (invalid input): every k
+            if (y_ok && lane == 0) set_error(p.err, ERR_BOUNDS);
+            x = m.ia;
+        }
+        m.x = x;
+        m.y = y;
+        return true;
+    };
+
+    // Issue the copies of chunk [k0, k0 + 32) of quadrant m into a slot.
+    auto issue = [&](const QMeta &m, int k0, int16_t *slot) {
+        const MergeJob jb = p.jobs[m.job];
+        const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
+        const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
+#pragma unroll 4
+        for (int c = lane; c < 2 * Q * (KC / 4); c += 32) {
+            const int row = c >> 3, piece = (c & 7) * 4;
+            const int k = k0 + piece;
+            const int16_t *src = row < Q ? U + row_elem<int16_t>(m.ia + row, k, NT)
+                                         : L + col_elem<int16_t>(k, m.ja + (row - Q));
+            cp_async8(slot + row * SP + piece, src);
+        }
+    };
+
+    // --- first staged quadrant
+    QMeta cur, nxt;
+    int cur_k0 = 0;
+    {
+        int64_t g;
+        while ((g = next_index()) >= 0 && !classify(g, cur)) {}
+        if (g < 0) return;
+        cur_k0 = cur.x & ~(KC - 1);
+        issue(cur, cur_k0, slots);
+        cp_async_commit();
+    }
+    int s = 0;
+    uint32_t acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
+
+    for (;;) {
+        int16_t *sl = slots + s * kSlotElems;
+        // The task after this one: the next chunk of this quadrant, or the
+        // first chunk of the next staged quadrant (constant ones are written
+        // as they are met).
+        bool more = true;
+        QMeta tm = cur;
+        int t_k0 = cur_k0 + KC;
+        if (t_k0 > cur.y) {
+            int64_t g;
+            while ((g = next_index()) >= 0 && !classify(g, nxt)) {}
+            if (g < 0) {
+                more = false;
+            } else {
+                tm = nxt;
+                t_k0 = nxt.x & ~(KC - 1);
+            }
+        }
+        if (more) issue(tm, t_k0, slots + (s ^ 1) * kSlotElems);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+
+        // Mask k < i (U), k > j (L) and k > n (both) where the chunk reaches them.
+        const int kmax = cur_k0 + KC - 1;
+        if (cur_k0 <= cur.ia + Q - 1 || kmax > cur.ja || kmax > n) {
+            const int i = cur.ia + lane, j = cur.ja + lane;
+            int16_t *ur = sl + lane * SP, *lr = sl + (Q + lane) * SP;
+#pragma unroll 8
+            for (int kk = 0; kk < KC; ++kk) {
+                const int k = cur_k0 + kk;
+                if (k < i || k > n) ur[kk] = kNeg;
+                if (k > j || k > n) lr[kk] = kNeg;
+            }
+            __syncwarp();
+        }
+        // (max,+) over this chunk's part of the band, 4 k per step.
+        const int lo = (max(cur.x, cur_k0) - cur_k0) & ~3;
+        const int hi = (min(cur.y, kmax) - cur_k0) | 3;
+        {
+            const int16_t *Ub = sl + ty * SP;
+            const int16_t *Lb = sl + (Q + tx) * SP;
+            uint2 u[8], lv[4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 4 * SP + lo);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) lv[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * SP + lo);
+            for (int kk = lo; kk <= hi; kk += 4) {
+                const int kn = kk + 4 <= hi ? kk + 4 : kk;
+                uint2 un[8], ln[4];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * 4 * SP + kn);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * SP + kn);
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = __viaddmax_s16x2(u[a].x, lv[b].x, acc[a][b]);
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = __viaddmax_s16x2(u[a].y, lv[b].y, acc[a][b]);
+#pragma unroll
+                for (int a = 0; a < 8; ++a) u[a] = un[a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) lv[b] = ln[b];
+            }
+        }
+        if (cur_k0 + KC > cur.y) {
+            // Last chunk of the quadrant: results through this slot.
+            __syncwarp();
+            write_quadrant(p.jobs[cur.job], cur.ia, cur.ja, acc, sl);
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
+        }
+        __syncwarp();
+        if (!more) break;
+        cur = tm;
+        cur_k0 = t_k0;
+        s ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace
+
+cudaError_t launch_quad_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
+    if (!p.sched || p.gshift != 5) return cudaErrorInvalidValue;
+    auto go = [&](auto kern) -> cudaError_t {
+        const size_t smem = (size_t)kQuadWarps * kWarpBytes;
+        cudaError_t e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQuadThreads, smem)) != cudaSuccess)
+            return e;
+        const int64_t NQ = (p.n + Q) / Q;
+        const int64_t work = p.njobs * NQ * (NQ + 1) / 2;
+        const int64_t warps = std::max<int64_t>(1, (int64_t)sms * std::max(per_sm, 1) * kQuadWarps);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, kQuadWarps),
+                                                                    (int64_t)sms * std::max(per_sm, 1)));
+        // Quadrants per grab: a few per warp amortise the counter; one when
+        // there are barely more quadrants than warps, to keep the tail short.
+        const int64_t per_warp = work / warps;
+        p.grab = per_warp >= 64 ? 4 : per_warp >= 16 ? 2 : 1;
+        return launch_pdl(kern, dim3((unsigned)grid), dim3(kQuadThreads), smem, st, p);
+    };
+    switch (out_dtype) {
+        case DT_I16: return go(quad_dpx_kernel<int16_t>);
+        case DT_I32: return go(quad_dpx_kernel<int32_t>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lcsg

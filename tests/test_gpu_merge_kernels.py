@@ -1,6 +1,7 @@
-"""Both tree merge kernels (exact refinement, DPX band product) give the
-oracle's DIST, length, LCS string and cross vertices, bit for bit
-(Sec. II-B-3); lcs_merge's exact argmax is unaffected by the selection.
+"""Every tree merge kernel (exact refinement, the DPX quadrant product, the
+DPX 64 x 64 tile product) gives the oracle's DIST, length, LCS string and
+cross vertices, bit for bit (Sec. II-B-3); lcs_merge's exact argmax is
+unaffected by the selection.
 
 The cases reuse the parity helpers; each kernel is selected on its own
 context with lcs_set_merge_kernel.
@@ -17,7 +18,7 @@ from test_gpu_parity import ALPH2, dist_buffer, gpu_dist, gpu_solve, oracle_dist
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX}
+KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX, "dpx_tile": B.LCS_MERGE_DPX_TILE}
 
 
 @pytest.fixture(scope="module", params=sorted(KINDS))
@@ -36,7 +37,7 @@ def test_set_merge_kernel_rejects_unknown():
     c = B.lcs_create(0, 0)
     try:
         with pytest.raises(B.LcsError):
-            B.lcs_set_merge_kernel(c, 3)
+            B.lcs_set_merge_kernel(c, 4)
         with pytest.raises(B.LcsError):
             B.lcs_set_merge_kernel(c, -1)
     finally:
@@ -96,6 +97,20 @@ def test_tree_dist_and_traceback(kctx, h):
         assert np.array_equal(gpu_dist(kctx, a, b, torch.int16, h=h), oracle_dist(a, b, torch.int16))
         s_want, v_want = oracle.traceback(a, b)
         s, cross, L = gpu_solve(kctx, a, b, h=h)
+        assert L == len(s_want) and s == s_want and np.array_equal(cross, v_want)
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 95, 96, 97, 159, 160, 161, 1023, 1024, 1025])
+def test_tree_ragged_quadrants(kctx, n):
+    """Widths around multiples of the 32-vertex quadrant and the 64-vertex
+    tile, three and more tree levels, both DIST types."""
+    rng = np.random.default_rng(5000 + n)
+    for m in (3 * 64 + 5, 8 * 64):
+        a, b = inputs.random_pair(rng, m, n, inputs.ACGT)
+        assert np.array_equal(gpu_dist(kctx, a, b, h=32), oracle_dist(a, b))
+        assert np.array_equal(gpu_dist(kctx, a, b, torch.int16, h=64), oracle_dist(a, b, torch.int16))
+        s_want, v_want = oracle.traceback(a, b)
+        s, cross, L = gpu_solve(kctx, a, b, h=32)
         assert L == len(s_want) and s == s_want and np.array_equal(cross, v_want)
 
 
