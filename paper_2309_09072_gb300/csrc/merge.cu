@@ -739,6 +739,8 @@ struct DpxMeta {
     int32_t cst;               // corner values agree: constant `val`
     int32_t val;
     int32_t valid;             // a tile of this CTA (else past the end)
+    int32_t va;                // D at the top-left corner (ia, ja)
+    int32_t ok;                // corners are a DIST merge's (else the band is every k)
 };
 
 template <typename TOut>
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
-    __shared__ int s_ok;
+    __shared__ int s_ok, s_x;
     __shared__ DpxMeta s_meta[32];
     __shared__ int64_t s_grab;
 
@@ -837,6 +839,8 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 // of the tile, [ia, ja + T - 1], and are flagged.
                 m.kl = ok ? klo : ia;
                 m.kh = ok ? min(khi, ja + T - 1) : min(ja + T - 1, n);
+                m.va = jb.vgrid[pa * (P + 1) + qa];
+                m.ok = ok ? 1 : 0;
                 if (!ok) set_error(p.err, ERR_BOUNDS);
             }
             s_meta[lane] = m;
@@ -866,7 +870,8 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 continue;
             }
             const int kt0 = m.kl >> T_SHIFT, ktop = m.kh >> T_SHIFT;
-            const int kbeg = m.kl & ~3, kend = m.kh | 3;
+            int kbeg = m.kl & ~3;
+            const int kend = m.kh | 3;
             uint32_t acc[8][4];
 #pragma unroll
             for (int a = 0; a < 8; ++a)
@@ -912,6 +917,31 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                     }
                 }
                 if (masked) __syncthreads();
+                if (m.ok && c0 == kt0 && c1 == ktop) {
+                    // The whole band is staged: narrow it to [x, kh], x the
+                    // largest maximiser of the corner (ia, ja) that is <= kh
+                    // (kh is the smallest maximiser of the far corner).  For
+                    // every entry (i, j) of the tile, a maximiser below x can
+                    // be replaced by x and one above kh by kh (Monge), so the
+                    // band keeps a maximiser of every entry.  U's row ia and
+                    // L's column ja are row 0 of the staged K-tiles.
+                    if (threadIdx.x < 32) {
+                        int x = -1;
+                        for (int t = min(m.kh, ja); t >= m.kl && x < 0; t -= 32) {
+                            const int k = t - lane;
+                            bool hit = false;
+                            if (k >= m.kl) {
+                                const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
+                                hit = (int)Us[o] + (int)Ls[o] == m.va;
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                            if (bal) x = t - (__ffs(bal) - 1);
+                        }
+                        if (lane == 0) s_x = x < 0 ? m.kl : x;
+                    }
+                    __syncthreads();
+                    kbeg = s_x & ~3;
+                }
                 for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
                     const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
                     const TIn *Ub = Us + (kt - c0) * EI + ty * PI;

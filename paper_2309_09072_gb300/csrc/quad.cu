@@ -59,9 +59,8 @@ constexpr int16_t kNeg = -16384;
 __device__ __forceinline__ int64_t gv(int64_t p, int64_t n) { return min(p << 5, n); }
 
 struct QMeta {
-    int job = 0, ia = 0, ja = 0;
-    int x = 0, y = -1;      // band; y < x: nothing staged
-    int valid = 0;
+    int job, ia, ja;        // merge of the launch, top-left vertex
+    int x, y;               // band of k
 };
 
 template <typename TOut>
@@ -131,9 +130,6 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
             }
         }
     };
-    auto write_const = [&](const MergeJob &jb, int ia, int ja, int v) {
-        store(jb, ia, ja, [&](int, int) { return v; });
-    };
     // The accumulators (the pair's two halves maximised) through the slot.
     auto write_quadrant = [&](const MergeJob &jb, int ia, int ja, uint32_t (&acc)[8][4], int16_t *sl) {
         TOut *st = reinterpret_cast<TOut *>(sl);
@@ -150,86 +146,150 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
         store(jb, ia, ja, [&](int x, int y) { return (int)st[x * SPO + y]; });
     };
 
-    // Quadrants come from the launch's counter, p.grab at a time.
-    int64_t q_next = 0, q_end = 0;
+    // Batches of quadrants: p.grab (1..32) consecutive quadrants from the
+    // launch's counter, classified a lane each -- corner values from the
+    // coarse grid, constant quadrants written at once, then x for four
+    // staged quadrants at a time (their scans' loads in flight together) --
+    // so that the latency of the loads is paid once per batch.  The staged
+    // ones are kept in this warp's part of shared memory.
+    QMeta *batch = reinterpret_cast<QMeta *>(smem + kQuadWarps * kWarpBytes) + warp * 32;
+    int b_pos = 0, b_len = 0;
     bool drained = false;
-    auto next_index = [&]() -> int64_t {
-        if (q_next >= q_end && !drained) {
-            unsigned g = 0;
-            if (lane == 0) g = atomicAdd(p.sched, (unsigned)p.grab);
-            g = __shfl_sync(0xffffffffu, g, 0);
-            q_next = g;
-            q_end = min((int64_t)g + (int64_t)p.grab, total);
-            drained = q_next >= total;
+    auto classify_batch = [&]() -> bool {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(p.sched, (unsigned)p.grab);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        const int64_t base = g0;
+        const int cnt = (int)max((int64_t)0, min((int64_t)p.grab, total - base));
+        if (cnt <= 0) return false;
+        QMeta m{0, 0, 0, 0, -1};
+        int va = 0, cval = 0;
+        bool cst = false, live = lane < cnt, y_ok = true;
+        if (live) {
+            const int64_t g = base + lane;
+            m.job = (int)(g / per_job);
+            const int64_t t = g - (int64_t)m.job * per_job;
+            int64_t lo = 0, hi = NQ - 1;                  // quadrant row: largest r with start(r) <= t
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (mid * NQ - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
+            }
+            const int I2 = (int)lo, J2 = (int)(lo + (t - (lo * NQ - lo * (lo - 1) / 2)));
+            m.ia = I2 * Q;
+            m.ja = J2 * Q;
+            const MergeJob jb = p.jobs[m.job];
+            const int64_t pa = I2, pb = min((int64_t)I2 + 1, P), qa = J2, qb = min((int64_t)J2 + 1, P);
+            int y = jb.kgrid[pb * (P + 1) + qb];
+            va = jb.vgrid[pa * (P + 1) + qa];
+            if (I2 < J2) {
+                // D is nonincreasing in i and nondecreasing in j: the
+                // quadrant's smallest value is at (ib, ja), its largest at (ia, jb).
+                const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
+                cst = vmin == vmax;
+                cval = vmax;
+            }
+            y_ok = y >= m.ia && y <= (int)gv(qb, n);
+            if (!y_ok) set_error(p.err, ERR_BOUNDS);
+            m.y = min(y_ok ? y : n, min(m.ja + Q - 1, n));
+            m.x = m.ia == m.ja ? m.ia : -1;               // on the diagonal, a's only k is ia
+            if (!y_ok) m.x = m.ia;                        // not a DIST merge's corners: every k
         }
-        return q_next < q_end ? q_next++ : -1;
+        // Constant quadrants, and the dense matrix's lower-left quadrant of
+        // each diagonal tile (no quadrant of the enumeration; written with
+        // the tile's odd diagonal quadrant), by the whole warp.
+        unsigned todo = __ballot_sync(0xffffffffu, live && cst);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const MergeJob jb = p.jobs[__shfl_sync(0xffffffffu, m.job, l)];
+            store(jb, __shfl_sync(0xffffffffu, m.ia, l), __shfl_sync(0xffffffffu, m.ja, l),
+                  [v = __shfl_sync(0xffffffffu, cval, l)](int, int) { return v; });
+        }
+        todo = __ballot_sync(0xffffffffu, live && m.ia == m.ja && ((m.ia >> 5) & 1));
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const MergeJob jb = p.jobs[__shfl_sync(0xffffffffu, m.job, l)];
+            if (jb.d_layout == LAYOUT_DENSE) {
+                const int ia = __shfl_sync(0xffffffffu, m.ia, l);
+                store(jb, ia, ia - Q, [](int, int) { return 0; });   // every entry has i > j
+            }
+        }
+        // x: the largest k <= y with U(ia, k) + L(k, ja) = D(a), k <= ja (the
+        // entries of a); four quadrants' first 32 candidates per round.
+        unsigned need = __ballot_sync(0xffffffffu, live && !cst && m.x < 0);
+        while (need) {
+            int ls[4], tops[4], vas[4], ias[4], jas[4];
+            const int16_t *us[4], *lsp[4];
+            int16_t fu[4], fl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ls[q] = -1;
+                if (need) {
+                    const int l = __ffs(need) - 1;
+                    need &= need - 1;
+                    ls[q] = l;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                fu[q] = fl[q] = 0;
+                if (ls[q] < 0) continue;                  // warp-uniform
+                const int l = ls[q];
+                const MergeJob jb = p.jobs[__shfl_sync(0xffffffffu, m.job, l)];
+                ias[q] = __shfl_sync(0xffffffffu, m.ia, l);
+                jas[q] = __shfl_sync(0xffffffffu, m.ja, l);
+                tops[q] = min(__shfl_sync(0xffffffffu, m.y, l), jas[q]);
+                vas[q] = __shfl_sync(0xffffffffu, va, l);
+                us[q] = reinterpret_cast<const int16_t *>(jb.U);
+                lsp[q] = reinterpret_cast<const int16_t *>(jb.L);
+                const int k = tops[q] - lane;
+                if (k >= ias[q]) {
+                    fu[q] = us[q][row_elem<int16_t>(ias[q], k, NT)];
+                    fl[q] = lsp[q][col_elem<int16_t>(k, jas[q])];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (ls[q] < 0) continue;
+                const int k = tops[q] - lane;
+                unsigned bal = __ballot_sync(0xffffffffu, k >= ias[q] && (int)fu[q] + (int)fl[q] == vas[q]);
+                int x = bal ? tops[q] - (__ffs(bal) - 1) : -1;
+                // Rarely the maximiser lies further down: 32 more at a time.
+                for (int top = tops[q] - 32; x < 0 && top >= ias[q]; top -= 32) {
+                    const int kk = top - lane;
+                    bool hit = false;
+                    if (kk >= ias[q])
+                        hit = (int)us[q][row_elem<int16_t>(ias[q], kk, NT)] +
+                                  (int)lsp[q][col_elem<int16_t>(kk, jas[q])] == vas[q];
+                    bal = __ballot_sync(0xffffffffu, hit);
+                    if (bal) x = top - (__ffs(bal) - 1);
+                }
+                if (x < 0) {                              // not a DIST's (invalid input): every k
+                    if (lane == 0) set_error(p.err, ERR_BOUNDS);
+                    x = ias[q];
+                }
+                if (lane == ls[q]) m.x = x;
+            }
+        }
+        // Keep the staged quadrants, in order.
+        const bool keep = live && !cst;
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+        if (keep) batch[__popc(kb & ((1u << lane) - 1u))] = m;
+        __syncwarp();
+        b_pos = 0;
+        b_len = __popc(kb);
+        return true;
     };
-
-    // Writes a constant quadrant, or classifies a staged one.  Returns false
-    // for a constant (or empty) quadrant.
-    auto classify = [&](int64_t g, QMeta &m) -> bool {
-        m.valid = 1;
-        m.job = (int)(g / per_job);
-        const int64_t t = g - (int64_t)m.job * per_job;
-        int64_t lo = 0, hi = NQ - 1;                      // quadrant row: largest r with start(r) <= t
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (mid * NQ - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
-        }
-        const int I2 = (int)lo, J2 = (int)(lo + (t - (lo * NQ - lo * (lo - 1) / 2)));
-        m.ia = I2 * Q;
-        m.ja = J2 * Q;
-        const MergeJob jb = p.jobs[m.job];
-        // The caller's dense matrix gets the sentinel below the diagonal:
-        // the fill kernels cover everything left of the diagonal 64 x 64
-        // tiles, and the lower-left quadrant of a diagonal tile (no quadrant
-        // of the enumeration) is written with the tile's odd diagonal one.
-        if (jb.d_layout == LAYOUT_DENSE && I2 == J2 && (I2 & 1))
-            store(jb, m.ia, m.ja - Q, [](int, int) { return 0; });   // every entry has i > j
-        const int64_t pa = I2, pb = min((int64_t)I2 + 1, P), qa = J2, qb = min((int64_t)J2 + 1, P);
-        const int ylim = min(m.ja + Q - 1, n);
-        int y = jb.kgrid[pb * (P + 1) + qb];
-        const int va = jb.vgrid[pa * (P + 1) + qa];
-        if (I2 < J2) {
-            // D is nonincreasing in i and nondecreasing in j: the quadrant's
-            // smallest value is at (ib, ja), its largest at (ia, jb).
-            const int vmin = jb.vgrid[pb * (P + 1) + qa], vmax = jb.vgrid[pa * (P + 1) + qb];
-            if (vmin == vmax) {
-                write_const(jb, m.ia, m.ja, vmax);
+    // The next staged quadrant of this warp (false: the launch is done).
+    auto next_quadrant = [&](QMeta &m) -> bool {
+        while (b_pos >= b_len) {
+            if (drained || !classify_batch()) {
+                drained = true;
                 return false;
             }
         }
-        const bool y_ok = y >= m.ia && y <= (int)gv(qb, n);
-        if (!y_ok) {
-            if (lane == 0) set_error(p.err, ERR_BOUNDS);
-            y = ylim;
-        }
-        y = min(y, ylim);
-        // x: the largest k <= y with U(ia, k) + L(k, ja) = D(a), scanning
-        // 32 k at a time downward (k <= ja, the entries of a).
-        int x = -1;
-        if (m.ia == m.ja) {
-            x = m.ia;                                    // a is on the diagonal: k = ia only
-        } else if (y_ok) {
-            const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
-            const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
-            for (int top = min(y, m.ja); top >= m.ia && x < 0; top -= 32) {
-                const int k = top - lane;
-                bool hit = false;
-                if (k >= m.ia) {
-                    const int f = (int)U[row_elem<int16_t>(m.ia, k, NT)] + (int)L[col_elem<int16_t>(k, m.ja)];
-                    hit = f == va;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (bal) x = top - (__ffs(bal) - 1);
-            }
-        }
-        if (x < 0) {                                     // not a DIST's (invalid input): every k
-            if (y_ok && lane == 0) set_error(p.err, ERR_BOUNDS);
-            x = m.ia;
-        }
-        m.x = x;
-        m.y = y;
+        m = batch[b_pos++];
         return true;
     };
 
@@ -252,9 +312,7 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
     QMeta cur, nxt;
     int cur_k0 = 0;
     {
-        int64_t g;
-        while ((g = next_index()) >= 0 && !classify(g, cur)) {}
-        if (g < 0) return;
+        if (!next_quadrant(cur)) return;
         cur_k0 = cur.x & ~(KC - 1);
         issue(cur, cur_k0, slots);
         cp_async_commit();
@@ -275,9 +333,7 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
         QMeta tm = cur;
         int t_k0 = cur_k0 + KC;
         if (t_k0 > cur.y) {
-            int64_t g;
-            while ((g = next_index()) >= 0 && !classify(g, nxt)) {}
-            if (g < 0) {
+            if (!next_quadrant(nxt)) {
                 more = false;
             } else {
                 tm = nxt;
@@ -357,7 +413,7 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
 cudaError_t launch_quad_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
     if (!p.sched || p.gshift != 5) return cudaErrorInvalidValue;
     auto go = [&](auto kern) -> cudaError_t {
-        const size_t smem = (size_t)kQuadWarps * kWarpBytes;
+        const size_t smem = (size_t)kQuadWarps * (kWarpBytes + 32 * sizeof(QMeta));
         cudaError_t e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -369,10 +425,11 @@ cudaError_t launch_quad_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
         const int64_t warps = std::max<int64_t>(1, (int64_t)sms * std::max(per_sm, 1) * kQuadWarps);
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, kQuadWarps),
                                                                     (int64_t)sms * std::max(per_sm, 1)));
-        // Quadrants per grab: a few per warp amortise the counter; one when
-        // there are barely more quadrants than warps, to keep the tail short.
+        // Quadrants per batch: a quarter of a warp's share (at most 32, a
+        // lane each), so that batches amortise the classification's load
+        // latency and still leave the tail short.
         const int64_t per_warp = work / warps;
-        p.grab = per_warp >= 64 ? 4 : per_warp >= 16 ? 2 : 1;
+        p.grab = (int32_t)std::max<int64_t>(1, std::min<int64_t>(32, per_warp / 4));
         return launch_pdl(kern, dim3((unsigned)grid), dim3(kQuadThreads), smem, st, p);
     };
     switch (out_dtype) {
