@@ -82,6 +82,10 @@ typedef struct {
     int32_t tree_levels;            /* merge levels above the strips             */
     int32_t kernel_launches;        /* kernels the last call launched            */
     int32_t tile;                   /* merge tile edge (vertices)                */
+    int32_t depth_first;            /* 1: the last call's tree was built depth
+                                       first (see lcs_set_schedule)              */
+    int32_t chunk_strips;           /* strips per strip launch of the last call  */
+    int64_t plan_bytes;             /* workspace the last call's plan needs      */
 } lcs_stats;
 
 /* Per-kernel-class timing of the calls made while profiling is on
@@ -156,6 +160,28 @@ lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
  * wait_limit_ns = 0 restore normal operation.  Errors: EINVAL (ctx NULL,
  * wait_limit_ns < 0). */
 lcs_status lcs_set_fault_injection(lcs_ctx *ctx, int32_t hold_band, int64_t wait_limit_ns);
+
+/* Order in which the tree of strips is built (Sec. II-A's recursion).
+ *   LCS_SCHED_AUTO    the retained tree when it needs at most 4 GiB and
+ *                     fits the budget, else depth first.
+ *   LCS_SCHED_RETAIN  breadth first: all strips in one launch, every merge
+ *                     of a tree level in one launch, and every node kept
+ *                     until the traceback has read it (fastest for small
+ *                     problems; memory (2S - 1) node triangles).
+ *   LCS_SCHED_DEPTH   depth first: `chunk` strips at a time (0: the largest
+ *                     of 8, 4, 2, 1 whose plan fits the budget), merged as
+ *                     soon as both halves exist, so that only the chunk's
+ *                     nodes and one pending node per tree level are alive;
+ *                     freed nodes are never re-read: the traceback
+ *                     recomputes, per node from the root down, the row of
+ *                     the upper child's DIST and the column of the lower
+ *                     child's that the path needs, by one bit-vector sweep
+ *                     each (Hirschberg's split), beside the tree on a side
+ *                     stream.  A call that wants no DIST builds no tree.
+ * The results do not depend on the schedule.  With an LCS wanted, a tree
+ * half of more than 16384 rows keeps the retained tree.  Errors: EINVAL. */
+enum { LCS_SCHED_AUTO = 0, LCS_SCHED_RETAIN = 1, LCS_SCHED_DEPTH = 2 };
+lcs_status lcs_set_schedule(lcs_ctx *ctx, int32_t mode, int32_t chunk);
 
 /* CUDA-graph replay of lcs_solve (1) or plain launches (0, the default).
  * With graphs on, the first lcs_solve with a given set of arguments runs as

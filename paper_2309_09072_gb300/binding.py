@@ -37,6 +37,9 @@ class lcs_stats(ctypes.Structure):
         ("tree_levels", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int32),
         ("tile", ctypes.c_int32),
+        ("depth_first", ctypes.c_int32),
+        ("chunk_strips", ctypes.c_int32),
+        ("plan_bytes", ctypes.c_int64),
     ]
 
 
@@ -110,6 +113,7 @@ def load(path: str = LIB_PATH):
             "lcs_set_merge_kernel": ([vp, i32], st),
             "lcs_set_graphs": ([vp, i32], st),
             "lcs_set_fault_injection": ([vp, i32, i64], st),
+            "lcs_set_schedule": ([vp, i32, i32], st),
             "lcs_autotune": ([vp, vp, i64, vp, i64, i32, vp, i64, vp, i64, vp, ctypes.POINTER(i32),
                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
@@ -250,6 +254,13 @@ LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX, LCS_MERGE_DPX_TILE = 0, 1, 2, 3
 
 def lcs_set_merge_kernel(ctx, kind: int) -> None:
     _check(ctx, load().lcs_set_merge_kernel(ctx, int(kind)))
+
+
+LCS_SCHED_AUTO, LCS_SCHED_RETAIN, LCS_SCHED_DEPTH = 0, 1, 2
+
+
+def lcs_set_schedule(ctx, mode: int, chunk: int = 0) -> None:
+    _check(ctx, load().lcs_set_schedule(ctx, int(mode), int(chunk)))
 
 
 def lcs_set_fault_injection(ctx, hold_band: bool, wait_limit_ns: int = 0) -> None:

@@ -65,9 +65,28 @@ struct Group {               // merges of one level launched together
     bool root;
 };
 
+// A launch of the depth-first schedule: strips [begin, begin + count) in one
+// strip launch, or merge group `begin`.
+struct Step {
+    bool strips;
+    int begin, count;
+};
+
 struct Plan {
     int64_t m = -1, n = -1;
     int h = 0, words = 1, S = 0, levels = 0, root = -1;
+    // Depth first (bounded memory): strips are built `chunk` at a time and
+    // merged as soon as both halves exist, nodes live in a pool of reused
+    // slots, and the traceback recomputes what it needs (recompute.cu).
+    bool depth_first = false;
+    int chunk = 0;
+    int pool_slots = 0;
+    std::vector<Step> steps;
+    std::vector<SweepNode> h_sweep;                  // merge nodes by depth from the root
+    std::vector<std::pair<int, int>> sweep_levels;   // top-down ranges in h_sweep
+    std::vector<int> sweep_rows;                     // tallest half per depth
+    size_t off_sweep = 0, off_fcnt = 0, off_bcnt = 0, off_counters = 0;
+    int max_depth_nodes = 0;
     bool dpx = false;        // every merge on the DPX (max,+) kernel, int16 nodes
     int64_t NT = 0, P = 0, P32 = 0;   // tiles per side; coarse-grid points at spacing 64 and 32
     int root_dt = DT_I32;    // dtype the root merge writes (caller's)
@@ -174,6 +193,11 @@ struct lcs_ctx {
     cudaMemPool_t mempool = nullptr;      // batches' device memory (stream ordered, no device sync)
     // solve_device: the root merge group beside the traceback
     cudaStream_t root_side = nullptr;
+    // depth-first solves: the recomputing traceback beside the tree
+    cudaStream_t tb_side = nullptr;
+    cudaEvent_t ev_tb_fork = nullptr, ev_tb = nullptr;
+    int32_t schedule = LCS_SCHED_AUTO, sched_chunk = 0;
+    std::vector<int64_t> sched_key;       // inputs of the current plan's schedule choice
     cudaEvent_t ev_fork = nullptr, ev_root = nullptr;
     // lcs_solve_host: DIST copied on a side stream while the traceback runs
     cudaStream_t side = nullptr;
@@ -267,6 +291,13 @@ lcs_status ensure_root_side(lcs_ctx *ctx) {
     if (!ctx->root_side) LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->root_side, cudaStreamNonBlocking));
     if (!ctx->ev_fork) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     if (!ctx->ev_root) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_root, cudaEventDisableTiming));
+    return LCS_OK;
+}
+
+lcs_status ensure_tb_side(lcs_ctx *ctx) {
+    if (!ctx->tb_side) LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->tb_side, cudaStreamNonBlocking));
+    if (!ctx->ev_tb_fork) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_tb_fork, cudaEventDisableTiming));
+    if (!ctx->ev_tb) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_tb, cudaEventDisableTiming));
     return LCS_OK;
 }
 
@@ -420,6 +451,226 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
     return P;
 }
 
+// Depth-first plan.  Strips are built `chunk` at a time; the strips of a
+// chunk are merged level by level into one node (one launch per level), and
+// that node enters a binary counter: while the counter holds a node of the
+// same level, the two are merged at once (the earlier rows are the upper
+// half).  At the end the counter's nodes are merged from the last rows up.
+// Every node is consumed by its parent right after it is made, so only the
+// chunk's nodes and one pending node per level are alive at a time; they
+// live in a pool of slots that the planner assigns by simulating the
+// launches (a merge's output slot is taken before its operands' slots are
+// released).  The root is the caller's dense matrix.  The tree's shape
+// differs from the breadth-first one when the strip count is not a power of
+// two; DIST is the same, and so is the LCS (the leftmost heaviest path does
+// not depend on the tree).
+Plan build_plan_depth_first(int64_t m, int64_t n, int h, int root_dt, int chunk) {
+    Plan P;
+    P.m = m; P.n = n; P.h = h; P.words = words_for(h); P.root_dt = root_dt;
+    P.S = (int)ceil_div(m, h);
+    P.NT = num_tiles_side(n);
+    P.P = ceil_div(n, T);
+    P.P32 = ceil_div(n, 32);
+    P.depth_first = true;
+    P.chunk = chunk = std::max(1, std::min(chunk, P.S));
+    for (int s = 0; s < P.S; ++s) {
+        Node nd;
+        nd.row0 = (int64_t)s * h;
+        nd.rows = std::min<int64_t>(h, m - nd.row0);
+        P.nodes.push_back(nd);
+    }
+    std::vector<Merge> merges;
+    auto merge = [&](int u, int l, int level) -> int {
+        Node nd;
+        nd.row0 = P.nodes[u].row0;
+        nd.rows = P.nodes[u].rows + P.nodes[l].rows;
+        nd.level = level;
+        P.nodes.push_back(nd);
+        const int out = (int)P.nodes.size() - 1;
+        Merge mg;
+        mg.u = u; mg.l = l; mg.out = out; mg.level = level;
+        P.nodes[u].parent = out; P.nodes[u].layout = LAYOUT_ROW;
+        P.nodes[l].parent = out; P.nodes[l].layout = LAYOUT_COL;
+        merges.push_back(mg);
+        return out;
+    };
+    std::vector<std::pair<int, int>> counter;      // (node, level)
+    std::vector<std::pair<int, int>> group_ranges;  // merge ranges launched together
+    for (int s0 = 0; s0 < P.S; s0 += chunk) {
+        const int cnt = std::min(chunk, P.S - s0);
+        P.steps.push_back(Step{true, s0, cnt});
+        std::vector<int> cur;
+        for (int s = s0; s < s0 + cnt; ++s) cur.push_back(s);
+        int level = 0;
+        while (cur.size() > 1) {
+            ++level;
+            std::vector<int> next;
+            const int gb = (int)merges.size();
+            for (size_t q = 0; q < cur.size(); q += 2)
+                next.push_back(q + 1 < cur.size() ? merge(cur[q], cur[q + 1], level) : cur[q]);
+            group_ranges.push_back({gb, (int)merges.size() - gb});
+            P.steps.push_back(Step{false, (int)group_ranges.size() - 1, 0});
+            cur.swap(next);
+        }
+        int node = cur[0];
+        while (!counter.empty() && counter.back().second == level) {
+            const int u = counter.back().first;
+            counter.pop_back();
+            ++level;
+            const int gb = (int)merges.size();
+            node = merge(u, node, level);
+            group_ranges.push_back({gb, 1});
+            P.steps.push_back(Step{false, (int)group_ranges.size() - 1, 0});
+        }
+        counter.push_back({node, level});
+    }
+    int node = counter.back().first;
+    int top = counter.back().second;
+    counter.pop_back();
+    while (!counter.empty()) {
+        const int u = counter.back().first;
+        top = std::max(top, counter.back().second) + 1;
+        counter.pop_back();
+        const int gb = (int)merges.size();
+        node = merge(u, node, top);
+        group_ranges.push_back({gb, 1});
+        P.steps.push_back(Step{false, (int)group_ranges.size() - 1, 0});
+    }
+    P.root = node;
+    P.nodes[P.root].root = true;
+    P.levels = 0;
+    for (auto &mg : merges) P.levels = std::max(P.levels, mg.level);
+    P.dpx = true;
+    for (auto &mg : merges)
+        if (std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows) > 16383) P.dpx = false;
+    for (auto &mg : merges) {
+        mg.in_dt = P.dpx ? (int)DT_I16 : dt_for(std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows));
+        P.nodes[mg.u].dtype = mg.in_dt;
+        P.nodes[mg.l].dtype = mg.in_dt;
+    }
+    for (auto &mg : merges) mg.out_dt = (mg.out == P.root) ? root_dt : P.nodes[mg.out].dtype;
+    P.merges = merges;
+    // Launch groups; a group whose merges differ in type is split.
+    std::vector<int> step_of_range(group_ranges.size());
+    {
+        std::vector<Step> steps;
+        for (const Step &st : P.steps) {
+            if (st.strips) { steps.push_back(st); continue; }
+            const auto rg = group_ranges[st.begin];
+            for (int q = rg.first; q < rg.first + rg.second;) {
+                const Merge &a = P.merges[q];
+                int e = q + 1;
+                while (e < rg.first + rg.second && P.merges[e].in_dt == a.in_dt && P.merges[e].out_dt == a.out_dt) ++e;
+                P.groups.push_back(Group{a.level, a.in_dt, a.out_dt, q, e - q, a.out == P.root});
+                steps.push_back(Step{false, (int)P.groups.size() - 1, 0});
+                q = e;
+            }
+        }
+        P.steps.swap(steps);
+    }
+    // Pool slots by simulation.
+    std::vector<int> slot(P.nodes.size(), -1), free_slots;
+    int nslots = 0;
+    auto take = [&]() { if (!free_slots.empty()) { int x = free_slots.back(); free_slots.pop_back(); return x; } return nslots++; };
+    size_t max_group = 1;
+    for (const Step &st : P.steps) {
+        if (st.strips) {
+            for (int s = st.begin; s < st.begin + st.count; ++s)
+                if (!P.nodes[s].root) slot[s] = take();
+            continue;
+        }
+        const Group &g = P.groups[st.begin];
+        max_group = std::max(max_group, (size_t)g.count);
+        for (int q = g.begin; q < g.begin + g.count; ++q)
+            if (P.merges[q].out != P.root) slot[P.merges[q].out] = take();
+        for (int q = g.begin; q < g.begin + g.count; ++q) {
+            free_slots.push_back(slot[P.merges[q].u]);
+            free_slots.push_back(slot[P.merges[q].l]);
+        }
+    }
+    P.pool_slots = nslots;
+    int max_dt_size = 1;
+    for (auto &nd : P.nodes) if (!nd.root) max_dt_size = std::max(max_dt_size, dt_size(nd.dtype));
+    const int slot_dt = max_dt_size == 4 ? DT_I32 : (max_dt_size == 2 ? DT_I16 : DT_U8);
+    const size_t slot_bytes = align256((size_t)num_tiles_tri(P.NT) * tile_elems(slot_dt) * dt_size(slot_dt));
+    size_t off = kHeaderBytes;
+    const size_t pool = off;
+    off += (size_t)nslots * slot_bytes;
+    for (size_t v = 0; v < P.nodes.size(); ++v)
+        if (!P.nodes[v].root) P.nodes[v].off = pool + (size_t)slot[v] * slot_bytes;
+    // Coarse grids: one per merge of the largest group, reused group after group.
+    const size_t kg_bytes = align256(2 * (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+    const size_t kg_base = off;
+    off += max_group * kg_bytes;
+    for (auto &g : P.groups)
+        for (int q = g.begin; q < g.begin + g.count; ++q) P.merges[q].kgrid_off = kg_base + (size_t)(q - g.begin) * kg_bytes;
+    P.off_counters = off; off = align256(off + sizeof(unsigned) * std::max<size_t>(1, P.groups.size()));
+    P.off_strip_outs = off; off = align256(off + sizeof(StripOut) * P.S);
+    P.off_jobs = off; off = align256(off + sizeof(MergeJob) * std::max<size_t>(1, P.merges.size()));
+    // Traceback by recompute: merge nodes by depth from the root.
+    std::vector<int> depth(P.nodes.size(), -1);
+    depth[P.root] = 0;
+    std::vector<int> order(P.merges.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    for (int q = (int)P.merges.size() - 1; q >= 0; --q) {      // parents after children in job order
+        const Merge &mg = P.merges[q];
+        depth[mg.u] = depth[mg.out] + 1;
+        depth[mg.l] = depth[mg.out] + 1;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return depth[P.merges[x].out] < depth[P.merges[y].out]; });
+    for (size_t q = 0; q < order.size();) {
+        size_t e = q + 1;
+        while (e < order.size() && depth[P.merges[order[e]].out] == depth[P.merges[order[q]].out]) ++e;
+        int rows = 0;
+        for (size_t t = q; t < e; ++t) {
+            const Merge &mg = P.merges[order[t]];
+            rows = std::max<int>(rows, (int)std::max(P.nodes[mg.u].rows, P.nodes[mg.l].rows));
+        }
+        P.sweep_levels.push_back({(int)q, (int)(e - q)});
+        P.sweep_rows.push_back(rows);
+        P.max_depth_nodes = std::max(P.max_depth_nodes, (int)(e - q));
+        q = e;
+    }
+    for (int q : order) {
+        const Merge &mg = P.merges[q];
+        SweepNode sn{};
+        sn.node = mg.out; sn.upper = mg.u; sn.lower = mg.l;
+        sn.r0 = (int32_t)P.nodes[mg.u].row0;
+        sn.rm = (int32_t)P.nodes[mg.l].row0;
+        sn.r1 = (int32_t)(P.nodes[mg.l].row0 + P.nodes[mg.l].rows);
+        P.h_sweep.push_back(sn);
+    }
+    P.off_sweep = off; off = align256(off + sizeof(SweepNode) * std::max<size_t>(1, P.h_sweep.size()));
+    P.off_fcnt = off; off = align256(off + (size_t)std::max(1, P.max_depth_nodes) * (n + 1) * 4);
+    P.off_bcnt = off; off = align256(off + (size_t)std::max(1, P.max_depth_nodes) * (n + 1) * 4);
+    P.off_tb = off; off = align256(off + sizeof(TbMerge));
+    P.off_path = off; off = align256(off + sizeof(int32_t) * 2 * P.nodes.size());
+    P.off_counts = off; off = align256(off + sizeof(int32_t) * 2 * P.S);
+    P.off_slots = off; off = align256(off + (size_t)P.S * h);
+    P.off_vbuf = off; off = align256(off + (size_t)(n + P.S + 1) * P.words * 4);
+    P.total = off;
+    P.h_jobs.resize(P.merges.size());
+    for (size_t q = 0; q < P.merges.size(); ++q) {
+        const Merge &mg = P.merges[q];
+        MergeJob j{};
+        j.U = reinterpret_cast<const void *>(P.nodes[mg.u].off);
+        j.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
+        j.D = (mg.out == P.root) ? nullptr : reinterpret_cast<void *>(P.nodes[mg.out].off);
+        j.kgrid = reinterpret_cast<int32_t *>(mg.kgrid_off);
+        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+        j.d_layout = (mg.out == P.root) ? LAYOUT_DENSE : P.nodes[mg.out].layout;
+        P.h_jobs[q] = j;
+    }
+    P.h_strip_outs.resize(P.S);
+    for (int s = 0; s < P.S; ++s) {
+        StripOut o{};
+        o.base = reinterpret_cast<void *>(P.nodes[s].off);
+        o.layout = P.nodes[s].layout;
+        P.h_strip_outs[s] = o;
+    }
+    return P;
+}
+
 template <typename X> X *reloc(char *base, X *off) {
     return reinterpret_cast<X *>(base + reinterpret_cast<uintptr_t>(off));
 }
@@ -481,7 +732,36 @@ std::vector<int64_t> tune_key(int64_t m, int64_t n, int root_dt) {
     return {lg(m), lg(n), (int64_t)root_dt};
 }
 
-lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
+// Retained (breadth-first) tree when it fits comfortably, else depth first
+// with the largest chunk of strips whose plan fits the budget.  Forced either
+// way by lcs_set_schedule.  The recomputing traceback sweeps a tree half of
+// at most sweep_max_rows() rows in one CTA, so a taller half keeps the
+// retained tree when an LCS is wanted.
+constexpr size_t kRetainLimit = (size_t)4 << 30;
+
+Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool want_tb) {
+    Plan R = build_plan(m, n, h, root_dt);
+    if (ctx->schedule == LCS_SCHED_RETAIN || R.S <= 1) return R;
+    const size_t room = ctx->budget > ctx->io_bytes ? ctx->budget - ctx->io_bytes : 0;
+    if (ctx->schedule == LCS_SCHED_AUTO && R.total <= std::min(room, kRetainLimit)) return R;
+    auto too_tall = [&](const Plan &D) {
+        for (auto &mg : D.merges)
+            if (std::max(D.nodes[mg.u].rows, D.nodes[mg.l].rows) > sweep_max_rows()) return true;
+        return false;
+    };
+    std::vector<int> chunks;
+    if (ctx->sched_chunk > 0) chunks.push_back(ctx->sched_chunk);
+    else chunks = {8, 4, 2, 1};
+    Plan D;
+    for (int c : chunks) {
+        D = build_plan_depth_first(m, n, h, root_dt, c);
+        if (want_tb && too_tall(D)) return R;
+        if (D.total <= room) return D;
+    }
+    return R.total <= room ? R : D;      // neither fits: ensure_workspace reports ENOMEM
+}
+
+lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb) {
     Plan &P = ctx->plan;
     int h = ctx->strip_h;
     ctx->tuned_merge = -1;
@@ -500,11 +780,18 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
     } else {
         ctx->auto_h = false;
     }
-    if (!(P.m == m && P.n == n && P.h == h && P.root_dt == root_dt)) {
-        // Kernels of an earlier call may still read the old descriptors.
-        LCS_CK(ctx, cudaDeviceSynchronize());
-        ctx->plan = build_plan(m, n, h, root_dt);
-        ctx->plan_uploaded = false;
+    const std::vector<int64_t> key = {m, n, h, root_dt, ctx->schedule, ctx->sched_chunk, want_tb ? 1 : 0,
+                                      (int64_t)ctx->budget};
+    if (key != ctx->sched_key || P.m < 0) {
+        Plan np = choose_plan(ctx, m, n, h, root_dt, want_tb);
+        if (!(P.m == m && P.n == n && P.h == h && P.root_dt == root_dt && P.depth_first == np.depth_first &&
+              P.chunk == np.chunk)) {
+            // Kernels of an earlier call may still read the old descriptors.
+            LCS_CK(ctx, cudaDeviceSynchronize());
+            ctx->plan = std::move(np);
+            ctx->plan_uploaded = false;
+        }
+        ctx->sched_key = key;
     }
     lcs_status s = ensure_workspace(ctx, ctx->plan.total);
     if (s != LCS_OK) return s;
@@ -528,6 +815,9 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
         }
         LCS_CK(ctx, cudaMemcpy(base + Q.off_strip_outs, so.data(), sizeof(StripOut) * so.size(),
                                cudaMemcpyHostToDevice));
+        if (!Q.h_sweep.empty())
+            LCS_CK(ctx, cudaMemcpy(base + Q.off_sweep, Q.h_sweep.data(), sizeof(SweepNode) * Q.h_sweep.size(),
+                                   cudaMemcpyHostToDevice));
         if (!jobs.empty()) {
             LCS_CK(ctx, cudaMemcpy(base + Q.off_jobs, jobs.data(), sizeof(MergeJob) * jobs.size(),
                                    cudaMemcpyHostToDevice));
@@ -554,6 +844,168 @@ lcs_status check_dense(lcs_ctx *ctx, const void *p, int64_t n, int64_t ld, int d
 }
 
 int api_dt(lcs_dtype d) { return d == LCS_I16 ? DT_I16 : DT_I32; }
+
+// The whole path with a depth-first plan.  The traceback needs only a and
+// b (it recomputes the rows and columns of freed nodes), so it runs on a side
+// stream from the start, beside the tree; the tree is built only when the
+// DIST is wanted.
+lcs_status solve_depth_first(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, int rdt,
+                             void *dist, int64_t ld, uint8_t *out_lcs, int64_t cap, int32_t *cross,
+                             int64_t *len_dev_out, bool want_tb, bool want_len, cudaStream_t st,
+                             cudaEvent_t dist_ready, bool early_fill) {
+    Plan &P = ctx->plan;
+    char *base = ctx->ws;
+    int *err = err_word(ctx);
+    int32_t *pathI = reinterpret_cast<int32_t *>(base + P.off_path);
+    int32_t *pathJ = pathI + P.nodes.size();
+    int32_t *counts = reinterpret_cast<int32_t *>(base + P.off_counts);
+    uint8_t *letters = reinterpret_cast<uint8_t *>(base + P.off_slots);
+    bool tb_forked = false, fill_side = false;
+    const int sentinel = rdt == DT_I16 ? INT16_MIN : INT32_MIN;
+
+    // 1. traceback / length: root down, per depth a sweep pair and a pick.
+    if (want_tb || want_len) {
+        lcs_status ss = ensure_tb_side(ctx);
+        if (ss != LCS_OK) return ss;
+        LCS_CK(ctx, cudaEventRecord(ctx->ev_tb_fork, st));
+        LCS_CK(ctx, cudaStreamWaitEvent(ctx->tb_side, ctx->ev_tb_fork, 0));
+        cudaStream_t ts = ctx->tb_side;
+        LCS_LAUNCHK(ctx, ts, K_TB, 0.0, 0.0, launch_root_path(pathI, pathJ, P.root, n, ts));
+        const SweepNode *sweep = reinterpret_cast<const SweepNode *>(base + P.off_sweep);
+        for (size_t d = 0; d < P.sweep_levels.size(); ++d) {
+            SweepParams sp{};
+            sp.nodes = sweep + P.sweep_levels[d].first;
+            sp.count = P.sweep_levels[d].second;
+            sp.root_node = P.root;
+            sp.a = a; sp.b = b; sp.n = n;
+            sp.pathI = pathI; sp.pathJ = pathJ;
+            sp.fcnt = reinterpret_cast<int32_t *>(base + P.off_fcnt);
+            sp.bcnt = reinterpret_cast<int32_t *>(base + P.off_bcnt);
+            sp.len_out = d == 0 ? len_word(ctx) : nullptr;
+            sp.err = err;
+            LCS_LAUNCHK(ctx, ts, K_TB, 0.0, 0.0, launch_node_sweep(sp, P.sweep_rows[d], ts));
+            LCS_LAUNCHK(ctx, ts, K_TB, 0.0, 0.0, launch_node_pick(sp, ts));
+            if (!want_tb) break;               // the root's maximum is the length
+        }
+        if (want_tb || P.S == 1) {
+            LeafParams lp{};
+            lp.a = a; lp.m = m; lp.h = P.h; lp.S = P.S; lp.b = b; lp.n = n;
+            lp.pathI = pathI; lp.pathJ = pathJ;
+            lp.vbuf = reinterpret_cast<uint32_t *>(base + P.off_vbuf);
+            lp.words = P.words; lp.slots = letters; lp.counts = counts; lp.cross = cross; lp.err = err;
+            LCS_LAUNCHK(ctx, ts, K_LEAF, 0.0, 0.0, launch_leaf(lp, ts));
+            CompactParams cp{};
+            cp.slots = letters; cp.counts = counts; cp.S = P.S; cp.h = P.h;
+            cp.out = out_lcs; cp.cap = cap; cp.len_out = len_word(ctx); cp.len_out2 = len_dev_out; cp.err = err;
+            LCS_LAUNCHK(ctx, ts, K_COMPACT, 0.0, 0.0, launch_compact(cp, ts));
+        } else if (len_dev_out) {
+            LCS_CK(ctx, launch_copy_len(len_word(ctx), len_dev_out, ts));
+        }
+        LCS_CK(ctx, cudaEventRecord(ctx->ev_tb, ts));
+        tb_forked = true;
+    }
+
+    // 2. the DIST tree, depth first.
+    if (dist) {
+        if (P.S == 1) {
+            StripParams sp{};
+            sp.a = a; sp.m = m; sp.h = P.h; sp.S = 1; sp.b = b; sp.n = n; sp.NT = P.NT;
+            sp.outs = nullptr; sp.dense = dist; sp.ld = ld; sp.band_first = 0;
+            LCS_LAUNCHK(ctx, st, K_STRIP, tri_entries(n) * dt_size(rdt), strip_ops(1, n, P.words),
+                        launch_strip(sp, rdt, P.words, st));
+            if (P.NT > 1)
+                LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                            launch_fill_dense(dist, rdt, n, ld, sentinel, 0, 0, nullptr, st));
+        } else {
+            if (early_fill) {
+                lcs_status ss = ensure_root_side(ctx);
+                if (ss != LCS_OK) return ss;
+                int sms = 0;
+                LCS_CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+                LCS_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+                LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_fork, 0));
+                LCS_LAUNCHK(ctx, ctx->root_side, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                            launch_fill_lower(dist, rdt, n, ld, sentinel, std::max(1, sms / 2), ctx->root_side));
+                LCS_CK(ctx, cudaEventRecord(ctx->ev_root, ctx->root_side));
+                fill_side = true;
+            }
+            unsigned int *counters = reinterpret_cast<unsigned int *>(base + P.off_counters);
+            LCS_CK(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned) * std::max<size_t>(1, P.groups.size()), st));
+            const StripOut *outs = reinterpret_cast<const StripOut *>(base + P.off_strip_outs);
+            const int64_t sigma0 = coarse_sigma0(P.P), sigma0_32 = coarse_sigma0(P.P32);
+            const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
+                           : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
+            for (const Step &stp : P.steps) {
+                if (stp.strips) {
+                    StripParams sp{};
+                    sp.a = a + (int64_t)stp.begin * P.h;
+                    sp.m = 0;
+                    for (int q = stp.begin; q < stp.begin + stp.count; ++q) sp.m += P.nodes[q].rows;
+                    sp.h = P.h; sp.S = stp.count; sp.b = b; sp.n = n; sp.NT = P.NT;
+                    sp.outs = outs + stp.begin; sp.dense = nullptr; sp.ld = 0; sp.band_first = 0;
+                    // The strips of a chunk share one dtype unless the last
+                    // chunk's short strip feeds a different merge type.
+                    bool same = true;
+                    for (int q = stp.begin; q < stp.begin + stp.count; ++q)
+                        if (P.nodes[q].dtype != P.nodes[stp.begin].dtype) same = false;
+                    if (same) {
+                        LCS_LAUNCHK(ctx, st, K_STRIP, stp.count * tri_entries(n) * dt_size(P.nodes[stp.begin].dtype),
+                                    strip_ops(stp.count, n, P.words),
+                                    launch_strip(sp, P.nodes[stp.begin].dtype, P.words, st));
+                    } else {
+                        for (int q = stp.begin; q < stp.begin + stp.count; ++q) {
+                            StripParams one = sp;
+                            one.a = a + (int64_t)q * P.h; one.m = P.nodes[q].rows; one.S = 1; one.outs = outs + q;
+                            LCS_LAUNCHK(ctx, st, K_STRIP, tri_entries(n) * dt_size(P.nodes[q].dtype),
+                                        strip_ops(1, n, P.words), launch_strip(one, P.nodes[q].dtype, P.words, st));
+                        }
+                    }
+                    continue;
+                }
+                const Group &g = P.groups[stp.begin];
+                const bool quad = P.dpx && (mk == LCS_MERGE_AUTO || mk == LCS_MERGE_DPX);
+                MergeParams mp{};
+                mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
+                mp.njobs = g.count;
+                mp.n = n; mp.NT = P.NT; mp.P = quad ? P.P32 : P.P; mp.ld = ld; mp.err = err;
+                mp.gshift = quad ? 5 : 0;
+                mp.dense_out = g.root ? dist : nullptr;
+                mp.dense_K = nullptr;
+                mp.const_tiles = 1;
+                mp.wait_ns = ctx->wait_ns; mp.hold_band = ctx->hold_band;
+                const int64_t sg0 = quad ? sigma0_32 : sigma0;
+                mp.sigma = (int32_t)sg0; mp.full = 1;
+                LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
+                for (int64_t sg = sg0 / 2; sg >= 1; sg /= 2) {
+                    mp.sigma = (int32_t)sg; mp.full = 0;
+                    LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
+                }
+                const double bytes = g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt));
+                if (P.dpx && mk != LCS_MERGE_EXACT) {
+                    mp.sched = counters + stp.begin;
+                    LCS_LAUNCHK(ctx, st, K_TILE, bytes, 0.0,
+                                quad ? launch_quad_dpx(mp, g.out_dt, st) : launch_tile_dpx(mp, g.out_dt, st));
+                } else {
+                    LCS_LAUNCHK(ctx, st, K_TILE, bytes, 0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, st));
+                    ctx->launches++;   // the pair is two kernel launches
+                }
+                if (g.root && !fill_side)
+                    LCS_LAUNCHK(ctx, st, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                                launch_fill_dense(dist, rdt, n, ld, sentinel, 0, 0, nullptr, st));
+            }
+            if (fill_side) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));
+        }
+        if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, st));
+    }
+    if (tb_forked) LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_tb, 0));   // join the traceback
+    ctx->stats.strip_height = P.h;
+    ctx->stats.strips = P.S;
+    ctx->stats.merges = (int32_t)P.merges.size();
+    ctx->stats.tree_levels = P.levels;
+    ctx->stats.kernel_launches = ctx->launches;
+    ctx->stats.tile = T;
+    return LCS_OK;
+}
 
 // The whole hot path on device buffers (see lcs_solve in lcs.h).
 // dist_ready (nullable): recorded once the dense DIST is complete, on the
@@ -601,9 +1053,15 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
         return LCS_OK;
     }
 
-    lcs_status s = prepare(ctx, m, n, rdt);
+    lcs_status s = prepare(ctx, m, n, rdt, want_tb);
     if (s != LCS_OK) return s;
     Plan &P = ctx->plan;
+    ctx->stats.depth_first = P.depth_first ? 1 : 0;
+    ctx->stats.chunk_strips = P.depth_first ? P.chunk : P.S;
+    ctx->stats.plan_bytes = (int64_t)P.total;
+    if (P.depth_first)
+        return solve_depth_first(ctx, a, m, b, n, rdt, dist, ld, out_lcs, cap, cross, len_dev_out, want_tb, want_len,
+                                 st, dist_ready, early_fill);
     char *base = ctx->ws;
     int *err = err_word(ctx);
     int32_t *pathI = reinterpret_cast<int32_t *>(base + P.off_path);
@@ -840,6 +1298,9 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->root_side) cudaStreamDestroy(ctx->root_side);
+    if (ctx->tb_side) cudaStreamDestroy(ctx->tb_side);
+    if (ctx->ev_tb_fork) cudaEventDestroy(ctx->ev_tb_fork);
+    if (ctx->ev_tb) cudaEventDestroy(ctx->ev_tb);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_root) cudaEventDestroy(ctx->ev_root);
     if (ctx->ev_dist) cudaEventDestroy(ctx->ev_dist);
@@ -874,6 +1335,14 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
     if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX_TILE) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
     ctx->merge_kernel = kind;
+    return LCS_OK;
+}
+
+lcs_status lcs_set_schedule(lcs_ctx *ctx, int32_t mode, int32_t chunk) {
+    if (!ctx || mode < LCS_SCHED_AUTO || mode > LCS_SCHED_DEPTH || chunk < 0)
+        return fail(ctx, LCS_EINVAL, "schedule arguments");
+    ctx->schedule = mode;
+    ctx->sched_chunk = chunk;
     return LCS_OK;
 }
 
@@ -1144,7 +1613,7 @@ lcs_status lcs_solve(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b
     std::vector<int64_t> key = {(int64_t)(uintptr_t)a, m, (int64_t)(uintptr_t)b, n, (int64_t)dtype,
                                 (int64_t)(uintptr_t)dist, ld, (int64_t)(uintptr_t)out_lcs, cap,
                                 (int64_t)(uintptr_t)cross, (int64_t)(uintptr_t)out_len_device,
-                                ctx->strip_h, ctx->merge_kernel, ctx->tune_gen};
+                                ctx->strip_h, ctx->merge_kernel, ctx->tune_gen, ctx->schedule, ctx->sched_chunk};
     // The captured kernels read the plan's descriptors from the workspace:
     // a graph stays valid only while that copy of the plan is the one it
     // was captured with.

@@ -154,6 +154,30 @@ cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st);
 // pathI[root] = 0, pathJ[root] = n: the whole path, source to sink.
 cudaError_t launch_root_path(int32_t *pathI, int32_t *pathJ, int32_t root, int64_t n, cudaStream_t st);
 
+// Traceback of a tree whose nodes were freed (recompute.cu): per depth, a
+// forward and a backward bit-vector sweep per node give one row of the upper
+// child's DIST and one column of the lower child's; the smallest maximiser
+// of their sum splits the node's sub-path.
+struct SweepNode {
+    int32_t node;          // merged node: its path endpoints pathI/pathJ[node]
+    int32_t upper, lower;  // its children
+    int32_t r0, rm, r1;    // rows: upper child [r0, rm), lower child [rm, r1)
+};
+struct SweepParams {
+    const SweepNode *nodes;  // the nodes of one depth (device array)
+    int32_t count;
+    int32_t root_node;
+    const uint8_t *a, *b;
+    int64_t n;
+    int32_t *pathI, *pathJ;
+    int32_t *fcnt, *bcnt;    // [count][n + 1] scratch: U(i, i + t), L(i + t, j)
+    int64_t *len_out;        // the root's maximum (the LCS length), nullable
+    int *err;
+};
+int sweep_max_rows();
+cudaError_t launch_node_sweep(const SweepParams &p, int max_rows, cudaStream_t st);
+cudaError_t launch_node_pick(const SweepParams &p, cudaStream_t st);
+
 struct LeafParams {
     const uint8_t *a;
     int64_t m;

@@ -1,0 +1,242 @@
+// recompute.cu -- the traceback of a tree whose nodes were not kept.
+//
+// When the merge tree is built depth first with bounded memory, a node's
+// DIST is freed once its parent has been merged, so the traceback cannot read
+// the children.  It recomputes what it needs instead, node by node from the
+// root down, as Hirschberg's split does: at a node covering rows [r0, r1)
+// whose part of the path runs from top vertex i to bottom vertex j, with the
+// halves split at row rm, the path crosses row rm at the smallest maximiser
+//     c = min argmax_{i <= k <= j} U(i, k) + L(k, j)            (Sec. II-D)
+// where U(i, k) = LCS(a[r0:rm], b[i:k]) is one row of the upper child's DIST
+// and L(k, j) = LCS(a[rm:r1], b[k:j]) one column of the lower child's.  Both
+// come from one bit-vector sweep each (the strip builder's column step):
+// forward over a[r0:rm] from column i, where the carry out of the top row at
+// column k is U(i, k) - U(i, k - 1), and backward over the reversed a[rm:r1]
+// against the reversed b[i:j], where after t columns the count is L(j - t, j).
+// The children then get (i, c) and (c, j); the strips at the bottom are
+// resolved by the leaf kernel as before.
+//
+// node_sweep_kernel: block 2q sweeps node q of one depth forward, block
+// 2q + 1 backward.  The vector is spread over NW warps of 32 lanes x 4 words
+// (up to 4096 NW rows); rows past the half's height never match, which
+// leaves the counts unchanged.  Within a warp the carries cross the lanes by
+// look-ahead on two ballots (generate, propagate), across warps through
+// shared memory with one named barrier per column.
+// node_pick_kernel: a CTA per node takes the smallest maximiser and hands the
+// two sub-paths down.
+#include <algorithm>
+
+#include "lcs_common.cuh"
+#include "lcs_kernels.h"
+
+namespace lcsg {
+
+namespace {
+
+constexpr int kRcWL = 4;                     // words per lane
+constexpr int kRcLetters = 32;               // distinct letters with a mask table
+
+template <int NW>
+struct RcCfg {
+    static constexpr int W = 32 * NW * kRcWL;                          // words of the vector
+    static constexpr size_t o_msk = 0;                                 // [kRcLetters][W]
+    static constexpr size_t o_a = o_msk + (size_t)kRcLetters * W * 4;  // the half's letters, sweep order
+    static constexpr size_t o_lmap = o_a + (size_t)W * 32;
+    static constexpr size_t o_present = o_lmap + 256;
+    static constexpr size_t o_xchg = o_present + 32;                   // [2][NW]
+    static constexpr size_t bytes = (o_xchg + 2 * NW * 4 + 15) / 16 * 16;
+};
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
+    pdl_wait_and_release();
+    using C = RcCfg<NW>;
+    constexpr int WL = kRcWL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t(*msk)[C::W] = reinterpret_cast<uint32_t(*)[C::W]>(smem_raw + C::o_msk);
+    uint8_t *sa = smem_raw + C::o_a;
+    uint8_t *lmap = smem_raw + C::o_lmap;
+    uint32_t *present = reinterpret_cast<uint32_t *>(smem_raw + C::o_present);
+    uint32_t *xchg = reinterpret_cast<uint32_t *>(smem_raw + C::o_xchg);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = blockIdx.x >> 1;
+    const bool back = (blockIdx.x & 1) != 0;
+    if (q >= p.count) return;
+    const SweepNode nd = p.nodes[q];
+    const int64_t n = p.n;
+    int64_t i = p.pathI[nd.node], j = p.pathJ[nd.node];
+    if (i < 0 || j > n || i > j) {                        // never for a consistent tree
+        if (tid == 0) set_error(p.err, ERR_BOUNDS);
+        i = j = 0;
+    }
+    const int r0 = back ? nd.rm : nd.r0, h = back ? nd.r1 - nd.rm : nd.rm - nd.r0;
+    if (h > 32 * C::W) {
+        if (tid == 0) set_error(p.err, ERR_BOUNDS);
+        return;
+    }
+    int32_t *cnt = (back ? p.bcnt : p.fcnt) + (int64_t)q * (n + 1);
+    const int64_t span = j - i;
+    // Rows in sweep order (backward: reversed), and the letters present.
+    if (tid < 8) present[tid] = 0u;
+    __syncthreads();
+    for (int r = tid; r < h; r += blockDim.x) {
+        const uint8_t ch = p.a[back ? r0 + h - 1 - r : r0 + r];
+        sa[r] = ch;
+        atomicOr(&present[ch >> 5], 1u << (ch & 31));
+    }
+    __syncthreads();
+    int nlet = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) nlet += __popc(present[t]);
+    const bool table = nlet <= kRcLetters;
+    const int Wu = (h + 31) >> 5;
+    if (table) {
+        for (int c = tid; c < 256; c += blockDim.x) {
+            const uint32_t word = present[c >> 5], bit = 1u << (c & 31);
+            int rank = 0;
+            for (int t = 0; t < (c >> 5); ++t) rank += __popc(present[t]);
+            rank += __popc(word & (bit - 1u));
+            lmap[c] = (word & bit) ? (uint8_t)rank : (uint8_t)255;
+        }
+        for (int t = tid; t < nlet * C::W; t += blockDim.x) (&msk[0][0])[t] = 0u;
+        __syncthreads();
+        for (int r = tid; r < h; r += blockDim.x) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
+    }
+    __syncthreads();
+    const int w0 = (warp * 32 + lane) * WL;
+    auto masks = [&](uint8_t ch, uint32_t (&M)[WL]) {
+        if (table) {
+            const uint8_t k = lmap[ch];
+#pragma unroll
+            for (int t = 0; t < WL; ++t) M[t] = (k == 255 || w0 + t >= Wu) ? 0u : msk[k][w0 + t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < WL; ++t) {
+                uint32_t mk = 0u;
+                const int rb = (w0 + t) * 32;
+                for (int b = 0; b < 32 && rb + b < h; ++b) mk |= (uint32_t)(sa[rb + b] == ch) << b;
+                M[t] = mk;
+            }
+        }
+    };
+    uint32_t V[WL];
+#pragma unroll
+    for (int t = 0; t < WL; ++t) V[t] = 0xFFFFFFFFu;
+    if (tid == 0) cnt[back ? span : 0] = 0;             // U(i, i) = 0, L(j, j) = 0
+    int dist = 0, par = 0;
+    // Sweep column t (1-based) takes b[i + t - 1] forward, b[j - t] backward.
+    auto letter_at = [&](int64_t t) -> uint32_t { return back ? p.b[j - t] : p.b[i + t - 1]; };
+    uint32_t bnext = (1 + lane <= span) ? letter_at(1 + lane) : 0u;
+    for (int64_t blk = 1; blk <= span; blk += 32) {
+        const uint32_t bcur = bnext;
+        bnext = (blk + 32 + lane <= span) ? letter_at(blk + 32 + lane) : 0u;
+        const int ncol = (int)min((int64_t)32, span - blk + 1);
+        int mine = 0;                                    // count after column blk + lane
+        for (int t = 0; t < ncol; ++t) {
+            const uint8_t ch = (uint8_t)__shfl_sync(0xFFFFFFFFu, bcur, t);
+            uint32_t M[WL], s[WL], u[WL];
+            masks(ch, M);
+#pragma unroll
+            for (int k = 0; k < WL; ++k) u[k] = V[k] & M[k];
+            const uint32_t carry = addn_cin<WL>(s, V, u, 0u);
+            uint32_t below[WL];
+            below[0] = 1u;
+#pragma unroll
+            for (int k = 1; k < WL; ++k) below[k] = below[k - 1] & (s[k - 1] == 0xFFFFFFFFu ? 1u : 0u);
+            const bool ones = (below[WL - 1] & (s[WL - 1] == 0xFFFFFFFFu ? 1u : 0u)) != 0u;
+            const uint32_t G = __ballot_sync(0xFFFFFFFFu, carry != 0u), Pb = __ballot_sync(0xFFFFFFFFu, ones);
+            const uint32_t A = G | Pb;
+            uint32_t cw = 0u, ctop;
+            if constexpr (NW == 1) {
+                ctop = (uint32_t)(((uint64_t)A + G) >> 32);
+            } else {
+                const uint32_t wg = (uint32_t)(((uint64_t)A + G) >> 32), wp = Pb == 0xFFFFFFFFu ? 1u : 0u;
+                if (lane == 0) xchg[par * NW + warp] = wg | (wp << 1);
+                named_bar_sync(1, NW * 32);
+                ctop = 0u;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t e = xchg[par * NW + w];
+                    const uint32_t cout = (e & 1u) | ((e >> 1) & ctop);
+                    if (w == warp) cw = ctop;
+                    ctop = cout;
+                }
+                par ^= 1;
+            }
+            const uint64_t S = (uint64_t)A + G + cw;
+            const uint32_t cin = (((uint32_t)S ^ A ^ G) >> lane) & 1u;
+            dist += (int)ctop;
+            if (lane == t) mine = dist;
+#pragma unroll
+            for (int k = 0; k < WL; ++k) V[k] = (s[k] + (cin & below[k])) | (V[k] & ~M[k]);
+        }
+        // Forward: U(i, i + blk + lane) at index blk + lane.  Backward:
+        // L(j - blk - lane, j) at index span - blk - lane.
+        if (warp == 0 && lane < ncol) cnt[back ? span - blk - lane : blk + lane] = mine;
+    }
+}
+
+__global__ void __launch_bounds__(256) node_pick_kernel(SweepParams p) {
+    pdl_wait_and_release();
+    __shared__ int sv[8];
+    __shared__ int64_t sk[8];
+    const int q = blockIdx.x;
+    const SweepNode nd = p.nodes[q];
+    const int64_t n = p.n;
+    int64_t i = p.pathI[nd.node], j = p.pathJ[nd.node];
+    if (i < 0 || j > n || i > j) i = j = 0;             // flagged by the sweep
+    const int32_t *f = p.fcnt + (int64_t)q * (n + 1), *g = p.bcnt + (int64_t)q * (n + 1);
+    int best = INT32_MIN;
+    int64_t bk = INT64_MAX;
+    for (int64_t k = i + threadIdx.x; k <= j; k += blockDim.x) {
+        const int v = f[k - i] + g[k - i];
+        if (v > best) { best = v; bk = k; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const int ov = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        const int64_t ok = __shfl_xor_sync(0xFFFFFFFFu, bk, off);
+        if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] > best || (sv[w] == best && sk[w] < bk)) { best = sv[w]; bk = sk[w]; }
+        const int32_t c = (int32_t)bk;
+        p.pathI[nd.upper] = (int32_t)i;
+        p.pathJ[nd.upper] = c;
+        p.pathI[nd.lower] = c;
+        p.pathJ[nd.lower] = (int32_t)j;
+        if (nd.node == p.root_node && p.len_out) *p.len_out = best;
+    }
+}
+
+template <int NW>
+cudaError_t launch_sweep_t(const SweepParams &p, cudaStream_t st) {
+    const size_t smem = RcCfg<NW>::bytes;
+    auto kern = node_sweep_kernel<NW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, dim3((unsigned)(2 * p.count)), dim3(NW * 32), smem, st, p);
+}
+
+}  // namespace
+
+int sweep_max_rows() { return 32 * RcCfg<4>::W; }
+
+cudaError_t launch_node_sweep(const SweepParams &p, int max_rows, cudaStream_t st) {
+    if (p.count <= 0) return cudaSuccess;
+    if (max_rows <= 32 * RcCfg<1>::W) return launch_sweep_t<1>(p, st);
+    if (max_rows <= 32 * RcCfg<2>::W) return launch_sweep_t<2>(p, st);
+    if (max_rows <= 32 * RcCfg<4>::W) return launch_sweep_t<4>(p, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_node_pick(const SweepParams &p, cudaStream_t st) {
+    if (p.count <= 0) return cudaSuccess;
+    return launch_pdl(node_pick_kernel, dim3((unsigned)p.count), dim3(256), 0, st, p);
+}
+
+}  // namespace lcsg
