@@ -49,11 +49,12 @@ namespace {
 constexpr int Q = 32;                       // quadrant edge
 constexpr int kQuadWarps = 4;               // warps per CTA, each independent
 constexpr int kQuadThreads = 32 * kQuadWarps;
-constexpr int KC = 32;                      // k per staged chunk
-constexpr int SP = KC + 4;                  // slot row pitch (elements): 72 bytes
+constexpr int KC = T;                       // k per staged chunk: one K-tile
+constexpr int SP = T + 4;                   // slot row pitch = the stored tile's (68 int16)
+constexpr int kHalfBytes = Q * SP * 2;      // 32 stored rows of a tile: 4352 contiguous bytes
 constexpr int kSlotElems = 2 * Q * SP;      // U rows then L rows
-constexpr int kSlotBytes = kSlotElems * 2;  // 4608
-constexpr int kWarpBytes = 2 * kSlotBytes;
+constexpr int kSlotBytes = kSlotElems * 2;  // 8704
+constexpr int kWarpBytes = 2 * kSlotBytes + 16;   // two slots and their two mbarriers
 constexpr int16_t kNeg = -16384;
 
 __device__ __forceinline__ int64_t gv(int64_t p, int64_t n) { return min(p << 5, n); }
@@ -64,11 +65,21 @@ struct QMeta {
 };
 
 template <typename TOut>
-__global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p) {
+__global__ void __launch_bounds__(kQuadThreads, 3) quad_dpx_kernel(MergeParams p) {
     pdl_wait_and_release();
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int16_t *slots = reinterpret_cast<int16_t *>(smem + warp * kWarpBytes);
+    constexpr int64_t EI16 = Fmt<int16_t>::ELEMS;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + warp * kWarpBytes + 2 * kSlotBytes);
+    const uint64_t lim = p.wait_ns ? p.wait_ns : kWaitLimitNs;
+    if (lane == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t phases = 0u, pend = 0u;          // bit t: slot t's barrier parity / a copy in flight
     const int n = (int)p.n;
     const int64_t NT = p.NT, P = p.P;
     const int64_t NQ = (n + Q) / Q;                         // quadrant rows: ceil((n+1) / 32)
@@ -293,19 +304,45 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
         return true;
     };
 
-    // Issue the copies of chunk [k0, k0 + 32) of quadrant m into a slot.
-    auto issue = [&](const QMeta &m, int k0, int16_t *slot) {
-        const MergeJob jb = p.jobs[m.job];
-        const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
-        const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
-#pragma unroll 4
-        for (int c = lane; c < 2 * Q * (KC / 4); c += 32) {
-            const int row = c >> 3, piece = (c & 7) * 4;
-            const int k = k0 + piece;
-            const int16_t *src = row < Q ? U + row_elem<int16_t>(m.ia + row, k, NT)
-                                         : L + col_elem<int16_t>(k, m.ja + (row - Q));
-            cp_async8(slot + row * SP + piece, src);
+    // Stage K-tile kt of quadrant m in slot sl: U's rows ia..ia+31 and L's
+    // columns ja..ja+31 of that K-tile are 32 consecutive stored rows each, so
+    // one TMA bulk copy apiece, completing on the slot's mbarrier.
+    auto issue = [&](const QMeta &m, int kt, int sl) {
+        if (lane == 0) {
+            const MergeJob jb = p.jobs[m.job];
+            const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
+            const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
+            int16_t *dst = slots + sl * kSlotElems;
+            fence_proxy_async_smem();            // the slot's last generic writes come first
+            mbar_arrive_expect_tx(bars + sl, 2u * kHalfBytes);
+            bulk_g2s(dst, U + row_tile(m.ia >> T_SHIFT, kt, NT) * EI16 + (m.ia & (T - 1)) * SP, kHalfBytes, bars + sl);
+            bulk_g2s(dst + Q * SP, L + col_tile(kt, m.ja >> T_SHIFT) * EI16 + (m.ja & (T - 1)) * SP, kHalfBytes,
+                     bars + sl);
         }
+        pend |= 1u << sl;
+    };
+    // Wait (bounded) for slot sl; on a timeout, flag it, give both slots'
+    // copies a second bounded wait so nothing lands after the warp leaves,
+    // and report false.
+    auto wait_slot = [&](int sl) -> bool {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(bars + sl, (phases >> sl) & 1u, lim) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0) {
+                set_error(p.err, ERR_TIMEOUT);
+                for (int t = 0; t < 2; ++t)
+                    if ((pend >> t) & 1u) mbar_wait_bounded(bars + t, (phases >> t) & 1u, lim);
+            }
+            __syncwarp();
+            return false;
+        }
+        // The phase has completed: every lane's own wait returns at once and
+        // makes the copied bytes visible to it.
+        if (lane != 0) mbar_wait_bounded(bars + sl, (phases >> sl) & 1u, lim);
+        phases ^= 1u << sl;
+        pend &= ~(1u << sl);
+        return true;
     };
 
     // --- first staged quadrant
@@ -314,8 +351,7 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
     {
         if (!next_quadrant(cur)) return;
         cur_k0 = cur.x & ~(KC - 1);
-        issue(cur, cur_k0, slots);
-        cp_async_commit();
+        issue(cur, cur_k0 >> T_SHIFT, 0);
     }
     int s = 0;
     uint32_t acc[8][4];
@@ -340,21 +376,26 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
                 t_k0 = nxt.x & ~(KC - 1);
             }
         }
-        if (more) issue(tm, t_k0, slots + (s ^ 1) * kSlotElems);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
+        if (more) issue(tm, t_k0 >> T_SHIFT, s ^ 1);
+        if (!wait_slot(s)) return;
 
-        // Mask k < i (U), k > j (L) and k > n (both) where the chunk reaches them.
+        // Mask k < i (U), k > j (L) and k > n (both) where the chunk reaches
+        // them (stored tiles hold unspecified values there).
         const int kmax = cur_k0 + KC - 1;
         if (cur_k0 <= cur.ia + Q - 1 || kmax > cur.ja || kmax > n) {
             const int i = cur.ia + lane, j = cur.ja + lane;
             int16_t *ur = sl + lane * SP, *lr = sl + (Q + lane) * SP;
-#pragma unroll 8
-            for (int kk = 0; kk < KC; ++kk) {
-                const int k = cur_k0 + kk;
-                if (k < i || k > n) ur[kk] = kNeg;
-                if (k > j || k > n) lr[kk] = kNeg;
+            for (int kk = 0; kk < KC; kk += 4) {
+                uint2 uu = *reinterpret_cast<uint2 *>(ur + kk), ll = *reinterpret_cast<uint2 *>(lr + kk);
+                int16_t *up = reinterpret_cast<int16_t *>(&uu), *lp = reinterpret_cast<int16_t *>(&ll);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = cur_k0 + kk + e;
+                    if (k < i || k > n) up[e] = kNeg;
+                    if (k > j || k > n) lp[e] = kNeg;
+                }
+                *reinterpret_cast<uint2 *>(ur + kk) = uu;
+                *reinterpret_cast<uint2 *>(lr + kk) = ll;
             }
             __syncwarp();
         }
@@ -405,7 +446,6 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
         cur_k0 = t_k0;
         s ^= 1;
     }
-    cp_async_wait<0>();
 }
 
 }  // namespace
@@ -413,8 +453,10 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad_dpx_kernel(MergeParams p
 cudaError_t launch_quad_dpx(MergeParams p, int out_dtype, cudaStream_t st) {
     if (!p.sched || p.gshift != 5) return cudaErrorInvalidValue;
     auto go = [&](auto kern) -> cudaError_t {
-        const size_t smem = (size_t)kQuadWarps * (kWarpBytes + 32 * sizeof(QMeta));
         cudaError_t e;
+        const size_t smem = (size_t)kQuadWarps * (kWarpBytes + 32 * sizeof(QMeta));
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
