@@ -392,7 +392,7 @@ def pair16384_measure(B, torch, peaks, peaks_src, steps=10):
                             "length + leftmost-argmax LCS", "value": m * n / (ms * 1e-3) / 1e9, "unit": "GCUPS",
                 "ms_per_step": ms, "steps": steps, "method_rate": method_rate(m, n, ms * 1e-3), "e2e": e2e,
                 "strip_height": stats["strip_height"],
-                "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_tile"}.get(tuned["merge_kernel"], "auto"),
+                "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_quad"}.get(tuned["merge_kernel"], "auto"),
                 "lcs_length": L, "peak_workspace_bytes": stats["peak_workspace_bytes"],
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in profile.items()},
                 "merge_roofline": merge}
@@ -621,7 +621,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_dict(args.variant, m, n),
             "tuning": {"strip_height": stats["strip_height"], "cuda_graphs": graphs,
-                       "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_tile"}.get(tuned["merge_kernel"], "auto"),
+                       "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_quad"}.get(tuned["merge_kernel"], "auto"),
                        "chosen_by": "lcs_autotune" if args.strip_height == 0 else "--strip-height"},
             "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
             "method_rate": method_rate(m, n, total_ms * 1e-3 / args.steps / world),

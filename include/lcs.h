@@ -132,18 +132,19 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
  *                       below the root), else LCS_MERGE_EXACT.
  *   LCS_MERGE_EXACT     Monge-windowed refinement of each 64 x 64 tile from
  *                       its corner maximisers, with the exact leftmost argmax.
- *   LCS_MERGE_DPX       (max,+) product of each 32 x 32 quadrant over the
- *                       band [x, y] between the largest maximiser x of its
- *                       top-left corner and the smallest y of its
- *                       bottom-right corner, on DPX instructions (D only),
- *                       one warp per quadrant; where the operands do not fit
- *                       int16, EXACT is used.
- *   LCS_MERGE_DPX_TILE  the same product per 64 x 64 tile over the band of
- *                       its corners' smallest maximisers (the earlier DPX
- *                       kernel, kept for comparison).
+ *   LCS_MERGE_DPX       (max,+) product of each 64 x 64 tile on DPX
+ *                       instructions (D only) over the band [x, y]: y the
+ *                       smallest maximiser of the tile's bottom-right corner,
+ *                       x the largest maximiser of its top-left corner that
+ *                       is <= y; where the operands do not fit int16, EXACT
+ *                       is used.
+ *   LCS_MERGE_DPX_QUAD  the same product per 32 x 32 quadrant, one warp per
+ *                       quadrant, from a coarse grid at spacing 32 (a third
+ *                       of the (max,+) terms of DPX, at the price of four
+ *                       times the coarse-grid points).
  * Applies to lcs_solve* and lcs_dist* on this ctx; lcs_merge, which returns
  * the argmax, always refines exactly.  Errors: EINVAL. */
-enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2, LCS_MERGE_DPX_TILE = 3 };
+enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2, LCS_MERGE_DPX_QUAD = 3 };
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
 
 /* Failure detection, for tests.  Every device-side wait of the merge
@@ -169,7 +170,8 @@ lcs_status lcs_set_fault_injection(lcs_ctx *ctx, int32_t hold_band, int64_t wait
  *                     until the traceback has read it (fastest for small
  *                     problems; memory (2S - 1) node triangles).
  *   LCS_SCHED_DEPTH   depth first: `chunk` strips at a time (0: the largest
- *                     of 8, 4, 2, 1 whose plan fits the budget), merged as
+ *                     of 32, 16, .., 1 whose plan fits both the budget and
+ *                     16 GiB, else the largest that fits the budget), merged as
  *                     soon as both halves exist, so that only the chunk's
  *                     nodes and one pending node per tree level are alive;
  *                     freed nodes are never re-read: the traceback

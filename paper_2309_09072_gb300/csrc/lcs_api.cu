@@ -733,11 +733,14 @@ std::vector<int64_t> tune_key(int64_t m, int64_t n, int root_dt) {
 }
 
 // Retained (breadth-first) tree when it fits comfortably, else depth first
-// with the largest chunk of strips whose plan fits the budget.  Forced either
-// way by lcs_set_schedule.  The recomputing traceback sweeps a tree half of
-// at most sweep_max_rows() rows in one CTA, so a taller half keeps the
-// retained tree when an LCS is wanted.
+// with the largest chunk of strips whose plan stays within both the budget
+// and kDepthTarget (larger chunks mean fewer, fuller launches: at m = n =
+// 16384 a chunk of 32 strips needs about 14 GB against the retained tree's
+// 36 GB).  Forced either way by lcs_set_schedule.  The recomputing
+// traceback sweeps a tree half of at most sweep_max_rows() rows in one CTA,
+// so a taller half keeps the retained tree when an LCS is wanted.
 constexpr size_t kRetainLimit = (size_t)4 << 30;
+constexpr size_t kDepthTarget = (size_t)16 << 30;
 
 Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool want_tb) {
     Plan R = build_plan(m, n, h, root_dt);
@@ -751,13 +754,17 @@ Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool wa
     };
     std::vector<int> chunks;
     if (ctx->sched_chunk > 0) chunks.push_back(ctx->sched_chunk);
-    else chunks = {8, 4, 2, 1};
+    else chunks = {32, 16, 8, 4, 2, 1};
+    const size_t target = ctx->sched_chunk > 0 ? room : std::min(room, kDepthTarget);
     Plan D;
     for (int c : chunks) {
+        if (c > R.S && c > 1 && ctx->sched_chunk == 0) continue;
         D = build_plan_depth_first(m, n, h, root_dt, c);
         if (want_tb && too_tall(D)) return R;
-        if (D.total <= room) return D;
+        if (D.total <= target) return D;
     }
+    // Nothing within the target: the smallest chunk that fits the budget.
+    if (D.total <= room) return D;
     return R.total <= room ? R : D;      // neither fits: ensure_workspace reports ENOMEM
 }
 
@@ -963,7 +970,7 @@ lcs_status solve_depth_first(lcs_ctx *ctx, const uint8_t *a, int64_t m, const ui
                     continue;
                 }
                 const Group &g = P.groups[stp.begin];
-                const bool quad = P.dpx && (mk == LCS_MERGE_AUTO || mk == LCS_MERGE_DPX);
+                const bool quad = P.dpx && mk == LCS_MERGE_DPX_QUAD;
                 MergeParams mp{};
                 mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
                 mp.njobs = g.count;
@@ -1156,7 +1163,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                            : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
             // The quadrant kernel reads the coarse grid at spacing 32, the
             // 64 x 64 tile kernels at spacing 64.
-            const bool quad = P.dpx && (mk == LCS_MERGE_AUTO || mk == LCS_MERGE_DPX);
+            const bool quad = P.dpx && mk == LCS_MERGE_DPX_QUAD;
             MergeParams mp{};
             mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
             mp.njobs = g.count;
@@ -1333,7 +1340,7 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
 }
 
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
-    if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX_TILE) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
+    if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX_QUAD) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
     ctx->merge_kernel = kind;
     return LCS_OK;
 }

@@ -1,5 +1,5 @@
-"""Every tree merge kernel (exact refinement, the DPX quadrant product, the
-DPX 64 x 64 tile product) gives the oracle's DIST, length, LCS string and
+"""Every tree merge kernel (exact refinement, the DPX 64 x 64 tile product,
+the DPX 32 x 32 quadrant product) gives the oracle's DIST, length, LCS string and
 cross vertices, bit for bit (Sec. II-B-3); lcs_merge's exact argmax is
 unaffected by the selection.
 
@@ -18,7 +18,7 @@ from test_gpu_parity import ALPH2, dist_buffer, gpu_dist, gpu_solve, oracle_dist
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX, "dpx_tile": B.LCS_MERGE_DPX_TILE}
+KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX, "dpx_quad": B.LCS_MERGE_DPX_QUAD}
 
 
 @pytest.fixture(scope="module", params=sorted(KINDS))
