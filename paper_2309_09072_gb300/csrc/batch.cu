@@ -65,8 +65,15 @@ __global__ void __launch_bounds__(BatchCfg<WPL>::kWarps * 32) batch_strip_kernel
     uint8_t *sa = ws + C::o_a;
     uint8_t *lmap = ws + C::o_lmap;
     uint32_t *present = reinterpret_cast<uint32_t *>(ws + C::o_present);
-    const int64_t warps = (int64_t)gridDim.x * C::kWarps;
-    for (int64_t q = (int64_t)blockIdx.x * C::kWarps + warp; q < bp.count; q += warps) {
+    // Pairs come from the batch's device work queue: each warp takes the next
+    // pair of the processing order (largest first) from an atomic counter as
+    // soon as it is free, so that pairs of very different costs spread over
+    // the warps as they finish.
+    for (;;) {
+        unsigned q32 = 0;
+        if (lane == 0) q32 = atomicAdd(bp.queue, 1u);
+        const int64_t q = (int64_t)__shfl_sync(0xFFFFFFFFu, q32, 0);
+        if (q >= bp.count) break;
         const BatchPair pr = bp.pairs[bp.order ? bp.order[q] : q];
         const int m = (int)pr.m;
         const int64_t n = pr.n;
@@ -294,6 +301,7 @@ static cudaError_t launch_wpl(const BatchParams &bp, cudaStream_t st) {
 
 cudaError_t launch_batch_strip(const BatchParams &bp, int wpl, cudaStream_t st) {
     if (bp.count <= 0) return cudaSuccess;
+    if (!bp.queue) return cudaErrorInvalidValue;
     switch (wpl) {
         case 2: return launch_wpl<2>(bp, st);
         case 4: return launch_wpl<4>(bp, st);

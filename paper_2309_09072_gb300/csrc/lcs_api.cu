@@ -1853,7 +1853,8 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     const size_t o_str = align256(o_err + sizeof(int));
     const size_t o_big = align256(o_str + (size_t)std::max<int64_t>(1, str_bytes));
     const size_t o_blens = align256(o_big + sizeof(BatchPair) * std::max<int64_t>(1, n_big));
-    const size_t o_scr = align256(o_blens + sizeof(int32_t) * std::max<int64_t>(1, n_big));
+    const size_t o_queue = align256(o_blens + sizeof(int32_t) * std::max<int64_t>(1, n_big));
+    const size_t o_scr = align256(o_queue + sizeof(unsigned) * kBatchClasses);
     const size_t total = align256(o_scr + (size_t)scr_words * 4);
     if (ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes + total > ctx->budget)
         return fail(ctx, LCS_EAGAIN, "batch does not fit the budget now");
@@ -1997,8 +1998,11 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         }
         // The classes run side by side, each on a stream forked from the
         // batch's; the tall pairs' kernels run on the batch's stream beside
-        // them; the classes join back before ev_done.
-        if (cudaEventRecord(t.lane.ev_fork, st) != cudaSuccess) {
+        // them; the classes join back before ev_done.  Each class's kernel
+        // pulls its pairs from a zeroed work-queue counter.
+        unsigned *queues = reinterpret_cast<unsigned *>(t.dev + o_queue);
+        if (cudaMemsetAsync(queues, 0, sizeof(unsigned) * kBatchClasses, st) != cudaSuccess ||
+            cudaEventRecord(t.lane.ev_fork, st) != cudaSuccess) {
             s = fail(ctx, LCS_ECUDA, "batch fork");
             break;
         }
@@ -2013,6 +2017,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             bp.scratch = scr;
             bp.strings = t.d_strings;
             bp.err = t.d_err;
+            bp.queue = queues + c;
             if (cudaStreamWaitEvent(t.lane.aux[c], t.lane.ev_fork, 0) != cudaSuccess ||
                 launch_batch_strip(bp, 2 << c, t.lane.aux[c]) != cudaSuccess ||
                 cudaEventRecord(t.lane.ev_join[c], t.lane.aux[c]) != cudaSuccess)

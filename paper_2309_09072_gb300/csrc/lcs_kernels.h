@@ -97,6 +97,7 @@ struct BatchParams {
     uint32_t *scratch;
     uint8_t *strings;
     int *err;
+    unsigned int *queue;   // work queue: the next position of `order` to take (zero at launch)
 };
 // The pairs of one words-per-lane class wpl (2, 4, 8 or 16: a up to
 // 1024 wpl rows) on one launch, a warp per pair.
