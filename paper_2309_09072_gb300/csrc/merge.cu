@@ -940,21 +940,29 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                             const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
                             return (int)Us[o + (i - ia) * PI] + (int)Ls[o + (j - ja) * PI];
                         };
-                        // y: smallest maximiser of b.
-                        int best = INT32_MIN, bk = INT32_MAX;
-                        for (int k = max(m.kl, bi) + lane; k <= min(m.kh, bj); k += 32) {
-                            const int v = f(bi, bj, k);
-                            if (v > best) { best = v; bk = k; }
+                        // y: smallest maximiser of b, and D(a) = the maximum
+                        // over a's own range, in one pass.
+                        int best = INT32_MIN, bk = INT32_MAX, va = INT32_MIN;
+                        const int lo = max(m.kl, ai);
+                        const int yb = max(m.kl, bi), ye = min(m.kh, bj), ae = min(m.kh, aj);
+                        for (int t = 0; yb + t <= ye || lo + t <= ae; t += 32) {
+                            const int ky = yb + t + lane, ka = lo + t + lane;
+                            if (ky <= ye) {
+                                const int v = f(bi, bj, ky);
+                                if (v > best) { best = v; bk = ky; }
+                            }
+                            if (ka <= ae) va = max(va, f(ai, aj, ka));
                         }
-                        warp_argmax(best, bk);
-                        yq = bk;
-                        // x: largest maximiser of a that is <= y (a's values
-                        // over its own range; a lane keeps its own up to 4).
-                        const int lo = max(m.kl, ai), hi = min(min(m.kh, aj), yq);
-                        int va = INT32_MIN;
-                        for (int k = lo + lane; k <= min(m.kh, aj); k += 32) va = max(va, f(ai, aj, k));
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) va = max(va, __shfl_xor_sync(0xffffffffu, va, off));
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const int ov = __shfl_xor_sync(0xffffffffu, best, off);
+                            const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
+                            if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
+                            va = max(va, __shfl_xor_sync(0xffffffffu, va, off));
+                        }
+                        yq = bk;
+                        // x: the largest maximiser of a that is <= y.
+                        const int hi = min(ae, yq);
                         int xk = -1;
                         for (int t = hi; t >= lo && xk < 0; t -= 32) {
                             const int k = t - lane;
@@ -992,13 +1000,24 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                             const int lo = max(qbeg, kt * T) & (T - 1), hi = min(qend, kt * T + T - 1) & (T - 1);
                             const TIn *Ub = Us + (kt - c0) * EI + r0 * PI;
                             const TIn *Lb = Ls + (kt - c0) * EI + cb * PI;
+                            uint2 un[2], ln[4];
+#pragma unroll
+                            for (int a = 0; a < 2; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * PI + lo);
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * PI + lo);
                             for (int kk = lo; kk <= hi; kk += 4) {
+                                // This step's operands were loaded one step
+                                // ahead; load the next step's now.
                                 uint2 u[2], lv[4];
 #pragma unroll
-                                for (int a = 0; a < 2; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * PI + kk);
+                                for (int a = 0; a < 2; ++a) u[a] = un[a];
 #pragma unroll
-                                for (int b = 0; b < 4; ++b)
-                                    lv[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * PI + kk);
+                                for (int b = 0; b < 4; ++b) lv[b] = ln[b];
+                                const int kn = kk + 4 <= hi ? kk + 4 : kk;
+#pragma unroll
+                                for (int a = 0; a < 2; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * PI + kn);
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * PI + kn);
 #pragma unroll
                                 for (int a = 0; a < 2; ++a)
 #pragma unroll
