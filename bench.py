@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--variant", choices=["iid", "correlated"], default="iid")
     ap.add_argument("--strip-height", type=int, default=0, help="0: autotuned")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA-graph replay")
+    ap.add_argument("--schedule", choices=["auto", "retain", "depth"], default="auto",
+                    help="tree schedule of the 4096 pair's solves (lcs_set_schedule)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -403,7 +405,7 @@ def pair16384_measure(B, torch, peaks, peaks_src, steps=10):
                             "length + leftmost-argmax LCS", "value": m * n / (ms * 1e-3) / 1e9, "unit": "GCUPS",
                 "ms_per_step": ms, "steps": steps, "method_rate": method_rate(m, n, ms * 1e-3), "e2e": e2e,
                 "strip_height": stats["strip_height"],
-                "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_quad"}.get(tuned["merge_kernel"], "auto"),
+                "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
                 "lcs_length": L, "peak_workspace_bytes": mem["peak_workspace_bytes"],
                 "schedule": {"depth_first": bool(mem["depth_first"]), "chunk_strips": mem["chunk_strips"],
                              "plan_bytes": mem["plan_bytes"],
@@ -556,6 +558,8 @@ def run_ours(args):
 
     ctx = B.lcs_create(local, 0)
     B.lcs_set_strip_height(ctx, args.strip_height)
+    B.lcs_set_schedule(ctx, {"auto": B.LCS_SCHED_AUTO, "retain": B.LCS_SCHED_RETAIN,
+                             "depth": B.LCS_SCHED_DEPTH}[args.schedule], 0)
     ad = torch.from_numpy(a.copy()).to(dev)
     bd = torch.from_numpy(b.copy()).to(dev)
     ld = ((n + 1) * 4 + 15) // 16 * 16 // 4
@@ -636,8 +640,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_dict(args.variant, m, n),
             "tuning": {"strip_height": stats["strip_height"], "cuda_graphs": graphs,
-                       "merge_kernel": {1: "exact", 2: "dpx", 3: "dpx_quad"}.get(tuned["merge_kernel"], "auto"),
-                       "chosen_by": "lcs_autotune" if args.strip_height == 0 else "--strip-height"},
+                       "merge_kernel": {1: "exact", 2: "dpx"}.get(tuned["merge_kernel"], "auto"),
+                       "chosen_by": "lcs_autotune" if args.strip_height == 0 else "--strip-height",
+                       "depth_first": bool(stats["depth_first"]), "plan_bytes": stats["plan_bytes"]},
             "e2e": e2e, "gpu_launches": stats["kernel_launches"] * args.steps,
             "method_rate": method_rate(m, n, total_ms * 1e-3 / args.steps / world),
             "roofline": roofline(profile, peaks, peaks_src, int_peak),

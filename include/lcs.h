@@ -138,13 +138,9 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h);
  *                       x the largest maximiser of its top-left corner that
  *                       is <= y; where the operands do not fit int16, EXACT
  *                       is used.
- *   LCS_MERGE_DPX_QUAD  the same product per 32 x 32 quadrant, one warp per
- *                       quadrant, from a coarse grid at spacing 32 (a third
- *                       of the (max,+) terms of DPX, at the price of four
- *                       times the coarse-grid points).
  * Applies to lcs_solve* and lcs_dist* on this ctx; lcs_merge, which returns
  * the argmax, always refines exactly.  Errors: EINVAL. */
-enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2, LCS_MERGE_DPX_QUAD = 3 };
+enum { LCS_MERGE_AUTO = 0, LCS_MERGE_EXACT = 1, LCS_MERGE_DPX = 2 };
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind);
 
 /* Failure detection, for tests.  Every device-side wait of the merge

@@ -249,7 +249,7 @@ def lcs_set_strip_height(ctx, h: int) -> None:
     _check(ctx, load().lcs_set_strip_height(ctx, int(h)))
 
 
-LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX, LCS_MERGE_DPX_QUAD = 0, 1, 2, 3
+LCS_MERGE_AUTO, LCS_MERGE_EXACT, LCS_MERGE_DPX = 0, 1, 2
 
 
 def lcs_set_merge_kernel(ctx, kind: int) -> None:

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcs_gb300.so")
-SOURCES = ["strip.cu", "merge.cu", "traceback.cu", "lcs_api.cu", "peak.cu", "noalloc.cu", "batch.cu", "batch_big.cu", "dform.cu", "quad.cu", "recompute.cu"]
+SOURCES = ["strip.cu", "merge.cu", "traceback.cu", "lcs_api.cu", "peak.cu", "noalloc.cu", "batch.cu", "batch_big.cu", "dform.cu", "recompute.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

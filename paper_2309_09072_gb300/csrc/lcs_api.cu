@@ -88,7 +88,7 @@ struct Plan {
     size_t off_sweep = 0, off_fcnt = 0, off_bcnt = 0, off_counters = 0;
     int max_depth_nodes = 0;
     bool dpx = false;        // every merge on the DPX (max,+) kernel, int16 nodes
-    int64_t NT = 0, P = 0, P32 = 0;   // tiles per side; coarse-grid points at spacing 64 and 32
+    int64_t NT = 0, P = 0;   // tiles per side; coarse-grid points per side - 1 (spacing 64)
     int root_dt = DT_I32;    // dtype the root merge writes (caller's)
     std::vector<Node> nodes;
     std::vector<Merge> merges;         // in job order
@@ -313,7 +313,6 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
     P.S = (int)ceil_div(m, h);
     P.NT = num_tiles_side(n);
     P.P = ceil_div(n, T);
-    P.P32 = ceil_div(n, 32);
     for (int s = 0; s < P.S; ++s) {
         Node nd;
         nd.row0 = (int64_t)s * h;
@@ -382,8 +381,8 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         off = align256(off + (size_t)tiles * tile_elems(nd.dtype) * dt_size(nd.dtype));
     }
     for (auto &mg : P.merges) {
-        mg.kgrid_off = off;                       // kgrid then vgrid, sized for spacing 32
-        off = align256(off + 2 * (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+        mg.kgrid_off = off;                       // kgrid then vgrid
+        off = align256(off + 2 * (size_t)(P.P + 1) * (P.P + 1) * 4);
     }
     P.off_strip_outs = off; off = align256(off + sizeof(StripOut) * P.S);
     P.off_jobs = off; off = align256(off + sizeof(MergeJob) * std::max<size_t>(1, P.merges.size()));
@@ -437,7 +436,7 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         j.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
         j.D = (mg.out == P.root) ? nullptr : reinterpret_cast<void *>(P.nodes[mg.out].off);
         j.kgrid = reinterpret_cast<int32_t *>(mg.kgrid_off);
-        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P + 1) * (P.P + 1) * 4);
         j.d_layout = (mg.out == P.root) ? LAYOUT_DENSE : P.nodes[mg.out].layout;
         P.h_jobs[q] = j;
     }
@@ -470,7 +469,6 @@ Plan build_plan_depth_first(int64_t m, int64_t n, int h, int root_dt, int chunk)
     P.S = (int)ceil_div(m, h);
     P.NT = num_tiles_side(n);
     P.P = ceil_div(n, T);
-    P.P32 = ceil_div(n, 32);
     P.depth_first = true;
     P.chunk = chunk = std::max(1, std::min(chunk, P.S));
     for (int s = 0; s < P.S; ++s) {
@@ -599,7 +597,7 @@ Plan build_plan_depth_first(int64_t m, int64_t n, int h, int root_dt, int chunk)
     for (size_t v = 0; v < P.nodes.size(); ++v)
         if (!P.nodes[v].root) P.nodes[v].off = pool + (size_t)slot[v] * slot_bytes;
     // Coarse grids: one per merge of the largest group, reused group after group.
-    const size_t kg_bytes = align256(2 * (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+    const size_t kg_bytes = align256(2 * (size_t)(P.P + 1) * (P.P + 1) * 4);
     const size_t kg_base = off;
     off += max_group * kg_bytes;
     for (auto &g : P.groups)
@@ -657,7 +655,7 @@ Plan build_plan_depth_first(int64_t m, int64_t n, int h, int root_dt, int chunk)
         j.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
         j.D = (mg.out == P.root) ? nullptr : reinterpret_cast<void *>(P.nodes[mg.out].off);
         j.kgrid = reinterpret_cast<int32_t *>(mg.kgrid_off);
-        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P32 + 1) * (P.P32 + 1) * 4);
+        j.vgrid = reinterpret_cast<int32_t *>(mg.kgrid_off + (size_t)(P.P + 1) * (P.P + 1) * 4);
         j.d_layout = (mg.out == P.root) ? LAYOUT_DENSE : P.nodes[mg.out].layout;
         P.h_jobs[q] = j;
     }
@@ -939,7 +937,7 @@ lcs_status solve_depth_first(lcs_ctx *ctx, const uint8_t *a, int64_t m, const ui
             unsigned int *counters = reinterpret_cast<unsigned int *>(base + P.off_counters);
             LCS_CK(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned) * std::max<size_t>(1, P.groups.size()), st));
             const StripOut *outs = reinterpret_cast<const StripOut *>(base + P.off_strip_outs);
-            const int64_t sigma0 = coarse_sigma0(P.P), sigma0_32 = coarse_sigma0(P.P32);
+            const int64_t sigma0 = coarse_sigma0(P.P);
             const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
                            : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
             for (const Step &stp : P.steps) {
@@ -970,17 +968,15 @@ lcs_status solve_depth_first(lcs_ctx *ctx, const uint8_t *a, int64_t m, const ui
                     continue;
                 }
                 const Group &g = P.groups[stp.begin];
-                const bool quad = P.dpx && mk == LCS_MERGE_DPX_QUAD;
                 MergeParams mp{};
                 mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
                 mp.njobs = g.count;
-                mp.n = n; mp.NT = P.NT; mp.P = quad ? P.P32 : P.P; mp.ld = ld; mp.err = err;
-                mp.gshift = quad ? 5 : 0;
-                mp.dense_out = g.root ? dist : nullptr;
+                mp.n = n; mp.NT = P.NT; mp.P = P.P; mp.ld = ld; mp.err = err;
+                    mp.dense_out = g.root ? dist : nullptr;
                 mp.dense_K = nullptr;
                 mp.const_tiles = 1;
                 mp.wait_ns = ctx->wait_ns; mp.hold_band = ctx->hold_band;
-                const int64_t sg0 = quad ? sigma0_32 : sigma0;
+                const int64_t sg0 = sigma0;
                 mp.sigma = (int32_t)sg0; mp.full = 1;
                 LCS_LAUNCHK(ctx, st, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, st));
                 for (int64_t sg = sg0 / 2; sg >= 1; sg /= 2) {
@@ -991,7 +987,7 @@ lcs_status solve_depth_first(lcs_ctx *ctx, const uint8_t *a, int64_t m, const ui
                 if (P.dpx && mk != LCS_MERGE_EXACT) {
                     mp.sched = counters + stp.begin;
                     LCS_LAUNCHK(ctx, st, K_TILE, bytes, 0.0,
-                                quad ? launch_quad_dpx(mp, g.out_dt, st) : launch_tile_dpx(mp, g.out_dt, st));
+                                launch_tile_dpx(mp, g.out_dt, st));
                 } else {
                     LCS_LAUNCHK(ctx, st, K_TILE, bytes, 0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, st));
                     ctx->launches++;   // the pair is two kernel launches
@@ -1142,7 +1138,7 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             }
         }
         // 2. merges, level by level
-        const int64_t sigma0 = coarse_sigma0(P.P), sigma0_32 = coarse_sigma0(P.P32);
+        const int64_t sigma0 = coarse_sigma0(P.P);
         int dpx_launch = 0;
         for (const Group &g : P.groups) {
             if (g.root && !dist) continue;
@@ -1161,19 +1157,15 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             }
             const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
                            : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
-            // The quadrant kernel reads the coarse grid at spacing 32, the
-            // 64 x 64 tile kernels at spacing 64.
-            const bool quad = P.dpx && mk == LCS_MERGE_DPX_QUAD;
             MergeParams mp{};
             mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
             mp.njobs = g.count;
-            mp.n = n; mp.NT = P.NT; mp.P = quad ? P.P32 : P.P; mp.ld = ld; mp.err = err;
-            mp.gshift = quad ? 5 : 0;
+            mp.n = n; mp.NT = P.NT; mp.P = P.P; mp.ld = ld; mp.err = err;
             mp.dense_out = g.root ? dist : nullptr;
             mp.dense_K = nullptr;
             mp.const_tiles = 1;
             mp.wait_ns = ctx->wait_ns; mp.hold_band = ctx->hold_band;
-            const int64_t sg0 = quad ? sigma0_32 : sigma0;
+            const int64_t sg0 = sigma0;
             mp.sigma = (int32_t)sg0; mp.full = 1;
             LCS_LAUNCHK(ctx, gs, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, gs));
             for (int64_t sg = sg0 / 2; sg >= 1; sg /= 2) {
@@ -1184,9 +1176,8 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 // A zeroed work counter per launch (zeroed above, once per solve).
                 mp.sched = dpx_launch < kSchedSlots ? sched + dpx_launch : nullptr;
                 ++dpx_launch;
-                if (quad && !mp.sched) return fail(ctx, LCS_EINVAL, "too many tree levels for the work counters");
                 LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, quad ? launch_quad_dpx(mp, g.out_dt, gs) : launch_tile_dpx(mp, g.out_dt, gs));
+                            0.0, launch_tile_dpx(mp, g.out_dt, gs));
             } else {
                 LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
                             0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, gs));
@@ -1340,7 +1331,7 @@ lcs_status lcs_set_strip_height(lcs_ctx *ctx, int32_t h) {
 }
 
 lcs_status lcs_set_merge_kernel(lcs_ctx *ctx, int32_t kind) {
-    if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX_QUAD) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
+    if (!ctx || kind < LCS_MERGE_AUTO || kind > LCS_MERGE_DPX) return fail(ctx, LCS_EINVAL, "unknown merge kernel");
     ctx->merge_kernel = kind;
     return LCS_OK;
 }

@@ -64,12 +64,6 @@ struct MergeParams {
     int32_t gshift;        // coarse grid spacing 2^gshift vertices (0: T = 64); P = ceil(n / 2^gshift)
 };
 
-// DPX (max,+) merge by 32 x 32 quadrants, each warp of a CTA on its own
-// quadrants (quad.cu).  Needs the coarse grid at spacing 32 (gshift = 5):
-// the band of a quadrant with corners a (top left) and b (bottom right) is
-// [x, y], y = K(b) and x the largest maximiser of a that is <= y.
-cudaError_t launch_quad_dpx(MergeParams p, int out_dtype, cudaStream_t st);
-
 // K-tiles per band for the main tile launch and the spill launch.
 int tile_cap_main(int in_dtype);
 int tile_cap_spill(int in_dtype, int out_dtype);

@@ -756,8 +756,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
-    __shared__ int s_ok;
-    __shared__ int s_band[4][2];               // per quadrant: [x, y], x > y: no work
+    __shared__ int s_ok, s_x;
     __shared__ DpxMeta s_meta[32];
     __shared__ int64_t s_grab;
 
@@ -871,8 +870,8 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 continue;
             }
             const int kt0 = m.kl >> T_SHIFT, ktop = m.kh >> T_SHIFT;
-            const int kbeg = m.kl & ~3, kend = m.kh | 3;
-            bool split = false;             // the tile went through the quadrant bands
+            int kbeg = m.kl & ~3;
+            const int kend = m.kh | 3;
             uint32_t acc[8][4];
 #pragma unroll
             for (int a = 0; a < 8; ++a)
@@ -919,123 +918,30 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 }
                 if (masked) __syncthreads();
                 if (m.ok && c0 == kt0 && c1 == ktop) {
-                    // The whole band is staged: each 32 x 32 quadrant of the
-                    // tile gets its own band [x, y] -- y the smallest
-                    // maximiser of its bottom-right entry b, x the largest
-                    // maximiser of its top-left entry a that is <= y.  For
-                    // every entry (i, j) of the quadrant a <= (i, j) <= b, so
-                    // by the Monge exchange a maximiser below x can be
-                    // replaced by x and one above y by y.  The four bands
-                    // hold about half the (max,+) terms of the tile's band.
-                    // Warp q finds quadrant q's band from the staged rows
-                    // and columns (all inside [kl, kh]).
-                    const int w = threadIdx.x >> 5;
-                    const int qi = w >> 1, qj = w & 1;
-                    const int ai = ia + 32 * qi, aj = ja + 32 * qj;
-                    const bool live = ai <= n && aj <= n && ai <= aj + 31;
-                    int xq = 1, yq = 0;
-                    if (live) {
-                        const int bi = min(ai + 31, n), bj = min(aj + 31, n);
-                        auto f = [&](int i, int j, int k) -> int {
-                            const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
-                            return (int)Us[o + (i - ia) * PI] + (int)Ls[o + (j - ja) * PI];
-                        };
-                        // y: smallest maximiser of b, and D(a) = the maximum
-                        // over a's own range, in one pass.
-                        int best = INT32_MIN, bk = INT32_MAX, va = INT32_MIN;
-                        const int lo = max(m.kl, ai);
-                        const int yb = max(m.kl, bi), ye = min(m.kh, bj), ae = min(m.kh, aj);
-                        for (int t = 0; yb + t <= ye || lo + t <= ae; t += 32) {
-                            const int ky = yb + t + lane, ka = lo + t + lane;
-                            if (ky <= ye) {
-                                const int v = f(bi, bj, ky);
-                                if (v > best) { best = v; bk = ky; }
-                            }
-                            if (ka <= ae) va = max(va, f(ai, aj, ka));
-                        }
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            const int ov = __shfl_xor_sync(0xffffffffu, best, off);
-                            const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
-                            if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
-                            va = max(va, __shfl_xor_sync(0xffffffffu, va, off));
-                        }
-                        yq = bk;
-                        // x: the largest maximiser of a that is <= y.
-                        const int hi = min(ae, yq);
-                        int xk = -1;
-                        for (int t = hi; t >= lo && xk < 0; t -= 32) {
+                    // The whole band is staged: narrow it to [x, kh], x the
+                    // largest maximiser of the corner (ia, ja) that is <= kh
+                    // (kh is the smallest maximiser of the far corner).  For
+                    // every entry (i, j) of the tile, a maximiser below x can
+                    // be replaced by x and one above kh by kh (Monge), so the
+                    // band keeps a maximiser of every entry.  U's row ia and
+                    // L's column ja are row 0 of the staged K-tiles.
+                    if (threadIdx.x < 32) {
+                        int x = -1;
+                        for (int t = min(m.kh, ja); t >= m.kl && x < 0; t -= 32) {
                             const int k = t - lane;
-                            const unsigned bal = __ballot_sync(0xffffffffu, k >= lo && f(ai, aj, k) == va);
-                            if (bal) xk = t - (__ffs(bal) - 1);
+                            bool hit = false;
+                            if (k >= m.kl) {
+                                const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
+                                hit = (int)Us[o] + (int)Ls[o] == m.va;
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                            if (bal) x = t - (__ffs(bal) - 1);
                         }
-                        if (yq == INT32_MAX || xk < 0) {
-                            // Not a DIST merge's operands: every k of the band.
-                            if (lane == 0) set_error(p.err, ERR_BOUNDS);
-                            xk = m.kl;
-                            yq = m.kh;
-                        }
-                        xq = xk;
-                    }
-                    if (lane == 0) {
-                        s_band[w][0] = xq;
-                        s_band[w][1] = yq;
+                        if (lane == 0) s_x = x < 0 ? m.kl : x;
                     }
                     __syncthreads();
-                    // Every warp takes 8 rows of every quadrant (rows
-                    // 8 w .. 8 w + 7 of it, all 32 columns), so the four
-                    // warps share each quadrant's band evenly: a lane owns
-                    // 2 rows x 4 columns (rows 2 ty, 2 ty + 1; columns
-                    // tx + 8 b).
-                    // The quadrant's results stay in acc[2 q + a][b] until Ds
-                    // is free (the previous tile's store may still read it).
-                    const int ty2 = lane >> 3, tx2 = lane & 7;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int bx = s_band[q][0], by = s_band[q][1];
-                        if (bx > by) continue;
-                        const int r0 = 32 * (q >> 1) + 8 * w + 2 * ty2, cb = 32 * (q & 1) + tx2;
-                        const int qbeg = bx & ~3, qend = by | 3;
-                        for (int kt = max(c0, qbeg >> T_SHIFT); kt <= min(c1, qend >> T_SHIFT); ++kt) {
-                            const int lo = max(qbeg, kt * T) & (T - 1), hi = min(qend, kt * T + T - 1) & (T - 1);
-                            const TIn *Ub = Us + (kt - c0) * EI + r0 * PI;
-                            const TIn *Lb = Ls + (kt - c0) * EI + cb * PI;
-                            uint2 un[2], ln[4];
-#pragma unroll
-                            for (int a = 0; a < 2; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * PI + lo);
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * PI + lo);
-                            for (int kk = lo; kk <= hi; kk += 4) {
-                                // This step's operands were loaded one step
-                                // ahead; load the next step's now.
-                                uint2 u[2], lv[4];
-#pragma unroll
-                                for (int a = 0; a < 2; ++a) u[a] = un[a];
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) lv[b] = ln[b];
-                                const int kn = kk + 4 <= hi ? kk + 4 : kk;
-#pragma unroll
-                                for (int a = 0; a < 2; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * PI + kn);
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 8 * PI + kn);
-#pragma unroll
-                                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                                    for (int b = 0; b < 4; ++b)
-                                        acc[2 * q + a][b] = __viaddmax_s16x2(u[a].x, lv[b].x, acc[2 * q + a][b]);
-#pragma unroll
-                                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                                    for (int b = 0; b < 4; ++b)
-                                        acc[2 * q + a][b] = __viaddmax_s16x2(u[a].y, lv[b].y, acc[2 * q + a][b]);
-                            }
-                        }
-                    }
-                    split = true;
-                } else
-                // A band wider than the staging buffer (several chunks) or
-                // corners that are not a DIST merge's: the product of the
-                // whole tile over the tile's band, chunk by chunk.
+                    kbeg = s_x & ~3;
+                }
                 for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
                     const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
                     const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
@@ -1094,24 +1000,15 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                     }
                 }
             }
-            {
-                // Entry (x, y) of acc[a][b]: whole-tile product, rows
-                // ty + 8 a and columns tx + 16 b; quadrant bands, quadrant
-                // q = a / 2, rows 32 (q / 2) + 8 w + 2 (lane / 8) + a % 2 and
-                // columns 32 (q % 2) + lane % 8 + 8 b.
-                const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
-                const int w = threadIdx.x >> 5;
+            const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
 #pragma unroll
-                for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int q = a >> 1;
-                        const int x = split ? 32 * (q >> 1) + 8 * w + 2 * (lane >> 3) + (a & 1) : ty + 8 * a;
-                        const int y = split ? 32 * (q & 1) + (lane & 7) + 8 * b : tx + 16 * b;
-                        const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
-                        Ds[x * ds_sx + y * ds_sy] = (TOut)v;
-                    }
-            }
+                for (int b = 0; b < 4; ++b) {
+                    const int x = ty + 8 * a, y = tx + 16 * b;
+                    const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+                    Ds[x * ds_sx + y * ds_sy] = (TOut)v;
+                }
             if (layout != LAYOUT_DENSE) fence_proxy_async_smem();
             __syncthreads();
             if (layout == LAYOUT_DENSE) {

@@ -1,5 +1,5 @@
-"""Every tree merge kernel (exact refinement, the DPX 64 x 64 tile product,
-the DPX 32 x 32 quadrant product) gives the oracle's DIST, length, LCS string and
+"""Both tree merge kernels (exact refinement, the DPX 64 x 64 tile band
+product) give the oracle's DIST, length, LCS string and
 cross vertices, bit for bit (Sec. II-B-3); lcs_merge's exact argmax is
 unaffected by the selection.
 
@@ -18,7 +18,7 @@ from test_gpu_parity import ALPH2, dist_buffer, gpu_dist, gpu_solve, oracle_dist
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX, "dpx_quad": B.LCS_MERGE_DPX_QUAD}
+KINDS = {"exact": B.LCS_MERGE_EXACT, "dpx": B.LCS_MERGE_DPX}
 
 
 @pytest.fixture(scope="module", params=sorted(KINDS))
@@ -37,7 +37,7 @@ def test_set_merge_kernel_rejects_unknown():
     c = B.lcs_create(0, 0)
     try:
         with pytest.raises(B.LcsError):
-            B.lcs_set_merge_kernel(c, 4)
+            B.lcs_set_merge_kernel(c, 3)
         with pytest.raises(B.LcsError):
             B.lcs_set_merge_kernel(c, -1)
     finally:
