@@ -19,9 +19,10 @@
 // node_sweep_kernel: block 2q sweeps node q of one depth forward, block
 // 2q + 1 backward.  The vector is spread over NW warps of 32 lanes x 4 words
 // (up to 4096 NW rows); rows past the half's height never match, which
-// leaves the counts unchanged.  Within a warp the carries cross the lanes by
-// look-ahead on two ballots (generate, propagate), across warps through
-// shared memory with one named barrier per column.
+// leaves the counts unchanged.  The sweep runs as a wavefront: lane g takes
+// column c at step c + g with the carry that lane g - 1 produced for the same
+// column one step earlier (a shuffle within a warp, shared memory and one
+// named barrier per step across warps).
 // node_pick_kernel: a CTA per node takes the smallest maximiser and hands the
 // two sub-paths down.
 #include <algorithm>
@@ -103,12 +104,31 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
         for (int r = tid; r < h; r += blockDim.x) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
     }
     __syncthreads();
-    const int w0 = (warp * 32 + lane) * WL;
+    // The sweep as a wavefront: lane g (of NW * 32) holds rows 128 g .. 128 g
+    // + 127 (4 words) and takes column c at step t = c + g, with the carry
+    // out of lane g - 1's words for the same column, made one step earlier
+    // (a shuffle within a warp; across warps through shared memory, one named
+    // barrier per step).  A column then costs one add-with-carry chain of 4
+    // words plus one shuffle on the critical path instead of a whole-vector
+    // carry resolution.  Lanes above the half's height only pass carries
+    // (their rows never match), so the carry out of the top lane that holds
+    // rows of the half, gtop, is the count's increment.
+    const int g = warp * 32 + lane;
+    const int gtop = min(NW * 32, (h + 127) >> 7) - 1;
+    const int w0 = g * WL;
     auto masks = [&](uint8_t ch, uint32_t (&M)[WL]) {
         if (table) {
             const uint8_t k = lmap[ch];
+            if (k == 255 || w0 >= Wu) {
 #pragma unroll
-            for (int t = 0; t < WL; ++t) M[t] = (k == 255 || w0 + t >= Wu) ? 0u : msk[k][w0 + t];
+                for (int t = 0; t < WL; ++t) M[t] = 0u;
+            } else {
+                const uint4 q = *reinterpret_cast<const uint4 *>(&msk[k][w0]);
+                M[0] = q.x; M[1] = q.y; M[2] = q.z; M[3] = q.w;
+#pragma unroll
+                for (int t = 0; t < WL; ++t)
+                    if (w0 + t >= Wu) M[t] = 0u;
+            }
         } else {
 #pragma unroll
             for (int t = 0; t < WL; ++t) {
@@ -119,60 +139,55 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
             }
         }
     };
+    // Sweep column c (1-based) takes b[i + c - 1] forward, b[j - c] backward.
+    auto letter_at = [&](int64_t c) -> uint8_t {
+        return (c >= 1 && c <= span) ? (back ? p.b[j - c] : p.b[i + c - 1]) : (uint8_t)0;
+    };
     uint32_t V[WL];
 #pragma unroll
     for (int t = 0; t < WL; ++t) V[t] = 0xFFFFFFFFu;
     if (tid == 0) cnt[back ? span : 0] = 0;             // U(i, i) = 0, L(j, j) = 0
-    int dist = 0, par = 0;
-    // Sweep column t (1-based) takes b[i + t - 1] forward, b[j - t] backward.
-    auto letter_at = [&](int64_t t) -> uint32_t { return back ? p.b[j - t] : p.b[i + t - 1]; };
-    uint32_t bnext = (1 + lane <= span) ? letter_at(1 + lane) : 0u;
-    for (int64_t blk = 1; blk <= span; blk += 32) {
-        const uint32_t bcur = bnext;
-        bnext = (blk + 32 + lane <= span) ? letter_at(blk + 32 + lane) : 0u;
-        const int ncol = (int)min((int64_t)32, span - blk + 1);
-        int mine = 0;                                    // count after column blk + lane
-        for (int t = 0; t < ncol; ++t) {
-            const uint8_t ch = (uint8_t)__shfl_sync(0xFFFFFFFFu, bcur, t);
-            uint32_t M[WL], s[WL], u[WL];
-            masks(ch, M);
+    int dist = 0;
+    uint32_t cout = 0u;
+    const int64_t steps = span + gtop;
+    // Operands one and two steps ahead: this lane's column at step t is t - g.
+    uint8_t ch1 = letter_at(1 - g), ch2 = letter_at(2 - g);
+    uint32_t Mn[WL];
+    masks(ch1, Mn);
+    for (int64_t t = 1; t <= steps; ++t) {
+        const int64_t c = t - g;
+        uint32_t cin = __shfl_up_sync(0xFFFFFFFFu, cout, 1);
+        if constexpr (NW > 1) {
+            if (lane == 0) cin = warp == 0 ? 0u : xchg[((t - 1) & 1) * NW + warp - 1];
+        } else {
+            if (lane == 0) cin = 0u;
+        }
+        uint32_t M[WL];
+#pragma unroll
+        for (int k = 0; k < WL; ++k) M[k] = Mn[k];
+        // The next step's mask and the letter after it load while this
+        // step's chain runs.
+        masks(ch2, Mn);
+        ch2 = letter_at(t + 2 - g);
+        const bool active = c >= 1 && c <= span && g <= gtop;
+        uint32_t co = 0u;
+        if (active) {
+            uint32_t u[WL], sum[WL];
 #pragma unroll
             for (int k = 0; k < WL; ++k) u[k] = V[k] & M[k];
-            const uint32_t carry = addn_cin<WL>(s, V, u, 0u);
-            uint32_t below[WL];
-            below[0] = 1u;
+            co = addn_cin<WL>(sum, V, u, cin);
 #pragma unroll
-            for (int k = 1; k < WL; ++k) below[k] = below[k - 1] & (s[k - 1] == 0xFFFFFFFFu ? 1u : 0u);
-            const bool ones = (below[WL - 1] & (s[WL - 1] == 0xFFFFFFFFu ? 1u : 0u)) != 0u;
-            const uint32_t G = __ballot_sync(0xFFFFFFFFu, carry != 0u), Pb = __ballot_sync(0xFFFFFFFFu, ones);
-            const uint32_t A = G | Pb;
-            uint32_t cw = 0u, ctop;
-            if constexpr (NW == 1) {
-                ctop = (uint32_t)(((uint64_t)A + G) >> 32);
-            } else {
-                const uint32_t wg = (uint32_t)(((uint64_t)A + G) >> 32), wp = Pb == 0xFFFFFFFFu ? 1u : 0u;
-                if (lane == 0) xchg[par * NW + warp] = wg | (wp << 1);
-                named_bar_sync(1, NW * 32);
-                ctop = 0u;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint32_t e = xchg[par * NW + w];
-                    const uint32_t cout = (e & 1u) | ((e >> 1) & ctop);
-                    if (w == warp) cw = ctop;
-                    ctop = cout;
-                }
-                par ^= 1;
+            for (int k = 0; k < WL; ++k) V[k] = sum[k] | (V[k] & ~M[k]);
+            if (g == gtop) {
+                dist += (int)co;
+                cnt[back ? span - c : c] = dist;   // U(i, i + c), or L(j - c, j)
             }
-            const uint64_t S = (uint64_t)A + G + cw;
-            const uint32_t cin = (((uint32_t)S ^ A ^ G) >> lane) & 1u;
-            dist += (int)ctop;
-            if (lane == t) mine = dist;
-#pragma unroll
-            for (int k = 0; k < WL; ++k) V[k] = (s[k] + (cin & below[k])) | (V[k] & ~M[k]);
         }
-        // Forward: U(i, i + blk + lane) at index blk + lane.  Backward:
-        // L(j - blk - lane, j) at index span - blk - lane.
-        if (warp == 0 && lane < ncol) cnt[back ? span - blk - lane : blk + lane] = mine;
+        cout = co;
+        if constexpr (NW > 1) {
+            if (lane == 31) xchg[(t & 1) * NW + warp] = co;
+            named_bar_sync(1, NW * 32);
+        }
     }
 }
 
