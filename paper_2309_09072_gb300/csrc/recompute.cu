@@ -45,7 +45,9 @@ struct RcCfg {
     static constexpr size_t o_lmap = o_a + (size_t)W * 32;
     static constexpr size_t o_present = o_lmap + 256;
     static constexpr size_t o_xchg = o_present + 32;                   // [2][NW]
-    static constexpr size_t bytes = (o_xchg + 2 * NW * 4 + 15) / 16 * 16;
+    static constexpr size_t o_b = (o_xchg + 2 * NW * 4 + 15) / 16 * 16;  // column letters, sweep order
+    static constexpr int kBCols = 16384;                                // staged when the span fits
+    static constexpr size_t bytes = o_b + kBCols + 64;
 };
 
 template <int NW>
@@ -59,6 +61,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     uint8_t *lmap = smem_raw + C::o_lmap;
     uint32_t *present = reinterpret_cast<uint32_t *>(smem_raw + C::o_present);
     uint32_t *xchg = reinterpret_cast<uint32_t *>(smem_raw + C::o_xchg);
+    uint8_t *sb = smem_raw + C::o_b;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = blockIdx.x >> 1;
     const bool back = (blockIdx.x & 1) != 0;
@@ -77,8 +80,13 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     }
     int32_t *cnt = (back ? p.bcnt : p.fcnt) + (int64_t)q * (n + 1);
     const int64_t span = j - i;
-    // Rows in sweep order (backward: reversed), and the letters present.
+    // Rows in sweep order (backward: reversed), and the letters present;
+    // the columns' letters in sweep order (sb[c] for column c, 1-based,
+    // sb[0] and past the span unused) when they fit.
     if (tid < 8) present[tid] = 0u;
+    const bool staged_b = span <= C::kBCols;
+    if (staged_b)
+        for (int c = tid; c < (int)span; c += blockDim.x) sb[c + 1] = back ? p.b[j - 1 - c] : p.b[i + c];
     __syncthreads();
     for (int r = tid; r < h; r += blockDim.x) {
         const uint8_t ch = p.a[back ? r0 + h - 1 - r : r0 + r];
@@ -89,8 +97,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     int nlet = 0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) nlet += __popc(present[t]);
-    const bool table = nlet <= kRcLetters;
-    const int Wu = (h + 31) >> 5;
+    const bool table = nlet < kRcLetters;            // one row kept clear for absent letters
     if (table) {
         for (int c = tid; c < 256; c += blockDim.x) {
             const uint32_t word = present[c >> 5], bit = 1u << (c & 31);
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
             rank += __popc(word & (bit - 1u));
             lmap[c] = (word & bit) ? (uint8_t)rank : (uint8_t)255;
         }
-        for (int t = tid; t < nlet * C::W; t += blockDim.x) (&msk[0][0])[t] = 0u;
+        for (int t = tid; t < min(nlet + 1, kRcLetters) * C::W; t += blockDim.x) (&msk[0][0])[t] = 0u;
         __syncthreads();
         for (int r = tid; r < h; r += blockDim.x) atomicOr(&msk[lmap[sa[r]]][r >> 5], 1u << (r & 31));
     }
@@ -116,19 +123,14 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     const int g = warp * 32 + lane;
     const int gtop = min(NW * 32, (h + 127) >> 7) - 1;
     const int w0 = g * WL;
+    // The table's rows are zero past the half's height (those bits are never set),
+    // and a lane above gtop never reads its mask; a letter absent from the
+    // half reads the zero row nlet (cleared with the others below).
     auto masks = [&](uint8_t ch, uint32_t (&M)[WL]) {
         if (table) {
             const uint8_t k = lmap[ch];
-            if (k == 255 || w0 >= Wu) {
-#pragma unroll
-                for (int t = 0; t < WL; ++t) M[t] = 0u;
-            } else {
-                const uint4 q = *reinterpret_cast<const uint4 *>(&msk[k][w0]);
-                M[0] = q.x; M[1] = q.y; M[2] = q.z; M[3] = q.w;
-#pragma unroll
-                for (int t = 0; t < WL; ++t)
-                    if (w0 + t >= Wu) M[t] = 0u;
-            }
+            const uint4 q = *reinterpret_cast<const uint4 *>(&msk[k == 255 ? nlet : k][min(w0, C::W - WL)]);
+            M[0] = q.x; M[1] = q.y; M[2] = q.z; M[3] = q.w;
         } else {
 #pragma unroll
             for (int t = 0; t < WL; ++t) {
@@ -140,8 +142,10 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
         }
     };
     // Sweep column c (1-based) takes b[i + c - 1] forward, b[j - c] backward.
-    auto letter_at = [&](int64_t c) -> uint8_t {
-        return (c >= 1 && c <= span) ? (back ? p.b[j - c] : p.b[i + c - 1]) : (uint8_t)0;
+    const int span32 = (int)span;
+    auto letter_at = [&](int c) -> uint8_t {
+        if (c < 1 || c > span32) return (uint8_t)0;
+        return staged_b ? sb[c] : (back ? p.b[j - c] : p.b[i + c - 1]);
     };
     uint32_t V[WL];
 #pragma unroll
@@ -149,13 +153,13 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     if (tid == 0) cnt[back ? span : 0] = 0;             // U(i, i) = 0, L(j, j) = 0
     int dist = 0;
     uint32_t cout = 0u;
-    const int64_t steps = span + gtop;
+    const int steps = span32 + gtop;
     // Operands one and two steps ahead: this lane's column at step t is t - g.
     uint8_t ch1 = letter_at(1 - g), ch2 = letter_at(2 - g);
     uint32_t Mn[WL];
     masks(ch1, Mn);
-    for (int64_t t = 1; t <= steps; ++t) {
-        const int64_t c = t - g;
+    for (int t = 1; t <= steps; ++t) {
+        const int c = t - g;
         uint32_t cin = __shfl_up_sync(0xFFFFFFFFu, cout, 1);
         if constexpr (NW > 1) {
             if (lane == 0) cin = warp == 0 ? 0u : xchg[((t - 1) & 1) * NW + warp - 1];
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
         // step's chain runs.
         masks(ch2, Mn);
         ch2 = letter_at(t + 2 - g);
-        const bool active = c >= 1 && c <= span && g <= gtop;
+        const bool active = c >= 1 && c <= span32 && g <= gtop;
         uint32_t co = 0u;
         if (active) {
             uint32_t u[WL], sum[WL];
