@@ -120,3 +120,40 @@ def test_schedule_rejects_bad_arguments(ctx):
         B.lcs_set_schedule(ctx, 3, 0)
     with pytest.raises(B.LcsError):
         B.lcs_set_schedule(ctx, B.LCS_SCHED_DEPTH, -1)
+
+
+@pytest.mark.parametrize("host", ["pinned", "pageable"])
+def test_solve_host_depth_first(ctx, host):
+    """lcs_solve_host on a depth-first plan: the pinned DIST's lower triangle
+    is filled on a side stream while the tree is built, the root merge writes
+    the rest over the link, and the traceback recomputes beside the tree."""
+    a, b = inputs.random_pair(np.random.default_rng(72), 1500, 1300)
+    m, n = len(a), len(b)
+    B.lcs_set_strip_height(ctx, 128)
+    ah = torch.from_numpy(a).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    dh = torch.full((n + 1, (n + 1 + 3) // 4 * 4), 5, dtype=torch.int32)
+    if host == "pinned":
+        dh = dh.pin_memory()
+    lh = torch.zeros(min(m, n), dtype=torch.uint8).pin_memory()
+    L = B.lcs_solve_host(ctx, ah, bh, dist_host=dh, lcs_host=lh)
+    assert B.lcs_get_stats(ctx)["depth_first"] == 1
+    s_want, _ = oracle.traceback(a, b)
+    assert L == len(s_want) and bytes(lh[:L].numpy()) == s_want
+    assert np.array_equal(dh[:, : n + 1].numpy().astype(np.int64), oracle_dist(a, b))
+
+
+def test_graph_replay_depth_first(ctx):
+    """CUDA-graph capture of a depth-first solve (side-stream fork and join
+    inside the capture) replays to the same results."""
+    a, b = inputs.random_pair(np.random.default_rng(73), 900, 1100)
+    B.lcs_set_graphs(ctx, True)
+    try:
+        for _ in range(3):                                  # eager, capture, replay
+            r = solve(ctx, a, b, h=64)
+            s_want, v_want = oracle.traceback(a, b)
+            assert r["stats"]["depth_first"] == 1
+            assert r["L"] == len(s_want) and r["s"] == s_want and np.array_equal(r["cross"], v_want)
+            assert np.array_equal(r["D"], oracle_dist(a, b))
+    finally:
+        B.lcs_set_graphs(ctx, False)
