@@ -299,6 +299,55 @@ static cudaError_t launch_wpl(const BatchParams &bp, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ pairs split in two
+// A CTA per split pair: the halves' columns from the split column c.
+__global__ void split_fix_kernel(const SplitPair *sp, int64_t count) {
+    const SplitPair s = sp[blockIdx.x];
+    if (threadIdx.x == 0) {
+        int64_t c = s.pathI[s.lower];
+        if (c < 0 || c > s.n) {
+            set_error(s.err, ERR_BOUNDS);
+            c = 0;
+        }
+        s.sub0->b = s.b;
+        s.sub0->n = c;
+        s.sub1->b = s.b + c;
+        s.sub1->n = s.n - c;
+    }
+    __syncthreads();
+    // A half on the tall kernels with its string keeps its cross vertices
+    // after its column vectors: m + 1 words set above any column.
+    for (int h = 0; h < 2; ++h) {
+        const BatchPair bp = h ? *s.sub1 : *s.sub0;
+        if (!(h ? s.big1 : s.big0) || !bp.want || bp.m <= 0 || bp.n <= 0) continue;
+        const int64_t wu = (bp.m + 31) / 32;
+        int32_t *v = reinterpret_cast<int32_t *>(s.scratch + bp.scratch_off + 2 * wu * (bp.n + 1));
+        for (int64_t r = threadIdx.x; r <= bp.m; r += blockDim.x) v[r] = 0x7F7F7F7F;
+    }
+}
+
+// A CTA per split pair: length = len0 + len1, the lower half's string after
+// the upper half's.
+__global__ void split_join_kernel(const SplitPair *sp, int64_t count) {
+    const SplitPair s = sp[blockIdx.x];
+    const int64_t l0 = *s.sub0->len_out, l1 = *s.sub1->len_out;
+    if (threadIdx.x == 0) *s.len_out = l0 + l1;
+    if (s.str && s.str1)
+        for (int64_t k = threadIdx.x; k < l1; k += blockDim.x) s.str[l0 + k] = s.str1[k];
+}
+
+cudaError_t launch_split_fix(const SplitPair *sp, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    split_fix_kernel<<<(unsigned)count, 256, 0, st>>>(sp, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_join(const SplitPair *sp, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    split_join_kernel<<<(unsigned)count, 256, 0, st>>>(sp, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_strip(const BatchParams &bp, int wpl, cudaStream_t st) {
     if (bp.count <= 0) return cudaSuccess;
     if (!bp.queue) return cudaErrorInvalidValue;

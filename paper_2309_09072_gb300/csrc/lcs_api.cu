@@ -1802,20 +1802,57 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     *ticket_out = 0;
     LCS_CK(ctx, cudaSetDevice(ctx->device));
     const int64_t max_rows = batch_max_rows();
-    // Layout of the batch's device block.
-    int64_t n_small = 0, n_big = 0, str_bytes = 0, scr_words = 0;
-    std::vector<int64_t> str_off(count, -1), scr_off(count, 0);
-    std::vector<char> big(count, 0);
+    // Work items: the caller's pairs, and for each pair with more rows than
+    // one strip but at most two strips' worth, its two halves split at row
+    // rm (the items count + 2 s and count + 2 s + 1 of split pair s).  A
+    // split pair's halves are one-strip pairs like the others; their columns
+    // come from the split column that the recomputing sweeps find on the
+    // device (Sec. II-D's argmax at the boundary row), and a join kernel adds
+    // the halves' lengths and appends the lower half's string to the upper's.
+    std::vector<lcs_pair> items(pairs, pairs + count);
+    std::vector<int64_t> split_parent, split_rm;            // per split pair
     for (int64_t q = 0; q < count; ++q) {
         const lcs_pair &pr = pairs[q];
-        if (pr.m < 0 || pr.n < 0 || (pr.m > 0 && !pr.a) || (pr.n > 0 && !pr.b))
-            return fail(ctx, LCS_EINVAL, "batch pair " + std::to_string(q) + ": bad string");
-        if (pr.m >= INT32_MAX / 2 || pr.n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "batch pair too long");
+        if (pr.m > max_rows && pr.m <= 2 * max_rows && pr.n > 0 && pr.a && pr.b) {
+            const int64_t rm = (pr.m + 1) / 2;
+            split_parent.push_back(q);
+            split_rm.push_back(rm);
+        }
+    }
+    const int64_t n_split = (int64_t)split_parent.size();
+    std::vector<char> is_split(count, 0);
+    for (int64_t k = 0; k < n_split; ++k) {
+        const lcs_pair &pr = pairs[split_parent[k]];
+        is_split[split_parent[k]] = 1;
+        lcs_pair h0 = pr, h1 = pr;
+        h0.m = split_rm[k];
+        h1.a = pr.a + split_rm[k];
+        h1.m = pr.m - split_rm[k];
+        items.push_back(h0);       // b, n: placeholders (the whole b) until the split is known
+        items.push_back(h1);
+    }
+    const int64_t nitems = (int64_t)items.size();
+    // Layout of the batch's device block.
+    int64_t n_small = 0, n_big = 0, str_bytes = 0, scr_words = 0;
+    std::vector<int64_t> str_off(nitems, -1), scr_off(nitems, 0);
+    std::vector<char> big(nitems, 0);
+    for (int64_t q = 0; q < nitems; ++q) {
+        const lcs_pair &pr = items[q];
+        if (q < count) {
+            if (pr.m < 0 || pr.n < 0 || (pr.m > 0 && !pr.a) || (pr.n > 0 && !pr.b))
+                return fail(ctx, LCS_EINVAL, "batch pair " + std::to_string(q) + ": bad string");
+            if (pr.m >= INT32_MAX / 2 || pr.n >= INT32_MAX / 2) return fail(ctx, LCS_EINVAL, "batch pair too long");
+        }
         const bool want = (pr.flags & LCS_WANT_STRING) != 0;
         if (want) {
-            str_off[q] = str_bytes;
-            str_bytes += std::min(pr.m, pr.n);
+            if (q >= count && ((q - count) & 1) == 0) {
+                str_off[q] = str_off[split_parent[(q - count) / 2]];   // the upper half writes the pair's slot
+            } else {
+                str_off[q] = str_bytes;                                // a pair, or a lower half's own slot
+                str_bytes += std::min(pr.m, pr.n);
+            }
         }
+        if (q < count && is_split[q]) continue;
         if (pr.m <= max_rows) {
             ++n_small;
             if (pr.m > kBatchBigRows && pr.n > 0) {
@@ -1838,14 +1875,31 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
         }
     }
     const size_t o_pairs = 0;
-    const size_t o_order = align256(o_pairs + sizeof(BatchPair) * std::max<int64_t>(1, count));
-    const size_t o_lens = align256(o_order + sizeof(int32_t) * std::max<int64_t>(1, count));
-    const size_t o_err = align256(o_lens + sizeof(int64_t) * std::max<int64_t>(1, count));
+    const size_t o_order = align256(o_pairs + sizeof(BatchPair) * std::max<int64_t>(1, nitems));
+    const size_t o_lens = align256(o_order + sizeof(int32_t) * std::max<int64_t>(1, nitems));
+    const size_t o_err = align256(o_lens + sizeof(int64_t) * std::max<int64_t>(1, nitems));
     const size_t o_str = align256(o_err + sizeof(int));
     const size_t o_big = align256(o_str + (size_t)std::max<int64_t>(1, str_bytes));
     const size_t o_blens = align256(o_big + sizeof(BatchPair) * std::max<int64_t>(1, n_big));
     const size_t o_queue = align256(o_blens + sizeof(int32_t) * std::max<int64_t>(1, n_big));
-    const size_t o_scr = align256(o_queue + sizeof(unsigned) * kBatchClasses);
+    // Split pairs: their descriptors, sweep nodes and pairs, path endpoints
+    // (nodes 3 s, 3 s + 1, 3 s + 2: the pair, its upper and lower half) and
+    // the sweeps' count rows.
+    int64_t split_nmax = 0;
+    int split_rows = 0;
+    for (int64_t k = 0; k < n_split; ++k) {
+        const lcs_pair &pr = pairs[split_parent[k]];
+        split_nmax = std::max(split_nmax, pr.n);
+        split_rows = std::max<int>(split_rows, (int)std::max(split_rm[k], pr.m - split_rm[k]));
+    }
+    const int64_t ns1 = std::max<int64_t>(1, n_split);
+    const size_t o_split = align256(o_queue + sizeof(unsigned) * kBatchClasses);
+    const size_t o_snode = align256(o_split + sizeof(SplitPair) * ns1);
+    const size_t o_spair = align256(o_snode + sizeof(SweepNode) * ns1);
+    const size_t o_spath = align256(o_spair + sizeof(SweepPair) * ns1);
+    const size_t o_fcnt = align256(o_spath + sizeof(int32_t) * 2 * 3 * ns1);
+    const size_t o_bcnt = align256(o_fcnt + sizeof(int32_t) * (size_t)(n_split ? n_split * (split_nmax + 1) : 1));
+    const size_t o_scr = align256(o_bcnt + sizeof(int32_t) * (size_t)(n_split ? n_split * (split_nmax + 1) : 1));
     const size_t total = align256(o_scr + (size_t)scr_words * 4);
     if (ctx->ws_bytes + ctx->io_bytes + ctx->batch_bytes + total > ctx->budget)
         return fail(ctx, LCS_EAGAIN, "batch does not fit the budget now");
@@ -1899,13 +1953,16 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     // last warps to finish have small ones.
     std::vector<BatchPair> hp;
     std::vector<int32_t> order;
+    // Where each half's descriptor goes: index in hp (>= 0) or -1 - index in hb.
+    std::vector<int64_t> half_desc(2 * n_split, 0);
     int64_t cls_begin[kBatchClasses + 1] = {0, 0, 0, 0, 0};
     for (int c = 0; c < kBatchClasses; ++c) {
         const int wpl = 2 << c;
         cls_begin[c] = (int64_t)hp.size();
-        for (int64_t q = 0; q < count; ++q) {
-            const lcs_pair &pr = pairs[q];
-            if (pr.m > max_rows || big[q] || batch_words_per_lane(pr.m) != wpl) continue;
+        for (int64_t q = 0; q < nitems; ++q) {
+            const lcs_pair &pr = items[q];
+            if ((q < count && is_split[q]) || pr.m > max_rows || big[q] || batch_words_per_lane(pr.m) != wpl) continue;
+            if (q >= count) half_desc[q - count] = (int64_t)hp.size();
             BatchPair b{};
             b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
             b.str_off = str_off[q] < 0 ? 0 : str_off[q];
@@ -1923,12 +1980,14 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     cls_begin[kBatchClasses] = (int64_t)hp.size();
     // Tall pairs that want their string, by words-per-lane class (8, 16).
     std::vector<BatchPair> hb;
+    std::vector<char> hb_half;
     int64_t big_begin[3] = {0, 0, 0}, big_max_n[2] = {0, 0};
     for (int g = 0; g < 2; ++g) {
         big_begin[g] = (int64_t)hb.size();
-        for (int64_t q = 0; q < count; ++q) {
-            const lcs_pair &pr = pairs[q];
+        for (int64_t q = 0; q < nitems; ++q) {
+            const lcs_pair &pr = items[q];
             if (!big[q] || batch_words_per_lane(pr.m) != (8 << g)) continue;
+            if (q >= count) half_desc[q - count] = -1 - (int64_t)hb.size();
             BatchPair b{};
             b.a = pr.a; b.b = pr.b; b.m = pr.m; b.n = pr.n;
             b.str_off = str_off[q] < 0 ? 0 : str_off[q];
@@ -1936,6 +1995,7 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             b.len_out = t.d_lens + q;
             b.want = str_off[q] >= 0 ? 1 : 0;
             hb.push_back(b);
+            hb_half.push_back(q >= count ? 1 : 0);
             big_max_n[g] = std::max(big_max_n[g], pr.n);
         }
     }
@@ -1944,14 +2004,14 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
     do {
         if (cudaEventRecord(t.lane.ev_start, st) != cudaSuccess ||
             cudaMemsetAsync(t.dev + o_err, 0, sizeof(int), st) != cudaSuccess ||
-            cudaMemsetAsync(t.d_lens, 0, sizeof(int64_t) * std::max<int64_t>(1, count), st) != cudaSuccess) {
+            cudaMemsetAsync(t.d_lens, 0, sizeof(int64_t) * std::max<int64_t>(1, nitems), st) != cudaSuccess) {
             s = fail(ctx, LCS_ECUDA, "batch setup");
             break;
         }
-        // Pairs too tall for one strip: the strip tree, one after another.
+        // Pairs taller than two strips: the strip tree, one after another.
         for (int64_t q = 0; q < count && s == LCS_OK; ++q) {
             const lcs_pair &pr = pairs[q];
-            if (pr.m <= max_rows) continue;
+            if (pr.m <= max_rows || is_split[q]) continue;
             lcs_status ps = solve_device(ctx, pr.a, pr.m, pr.b, pr.n, LCS_I32, nullptr, 0,
                                          str_off[q] >= 0 ? t.d_strings + str_off[q] : nullptr,
                                          std::min(pr.m, pr.n), nullptr, t.d_lens + q, true, st);
@@ -1975,8 +2035,9 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
                 s = fail(ctx, LCS_ECUDA, "batch tall descriptors");
                 break;
             }
-            for (const BatchPair &b : hb) {
-                if (!b.want) continue;
+            for (size_t x = 0; x < hb.size(); ++x) {
+                const BatchPair &b = hb[x];
+                if (!b.want || hb_half[x]) continue;         // a half's are set by the split kernel
                 const int64_t wu = (b.m + 31) / 32;
                 // Cross vertices start above any column (0x7F7F7F7F > n).
                 if (cudaMemsetAsync(scr + b.scratch_off + 2 * wu * (b.n + 1), 0x7F, sizeof(int32_t) * (b.m + 1), st) !=
@@ -1986,6 +2047,69 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
                 }
             }
             if (s != LCS_OK) break;
+        }
+        // Split pairs: the root's forward and backward sweeps (a CTA each per
+        // pair), the smallest maximiser per pair (the split column), then the
+        // halves' columns in their descriptors, before any class kernel runs.
+        if (n_split > 0) {
+            std::vector<SplitPair> hs(n_split);
+            std::vector<SweepNode> hn(n_split);
+            std::vector<SweepPair> hq(n_split);
+            std::vector<int32_t> hpath(2 * 3 * n_split, 0);
+            int32_t *pathI = reinterpret_cast<int32_t *>(t.dev + o_spath), *pathJ = pathI + 3 * n_split;
+            auto desc = [&](int64_t h) -> BatchPair * {
+                const int64_t x = half_desc[h];
+                return x >= 0 ? reinterpret_cast<BatchPair *>(t.dev + o_pairs) + x
+                              : reinterpret_cast<BatchPair *>(t.dev + o_big) + (-1 - x);
+            };
+            for (int64_t k = 0; k < n_split; ++k) {
+                const int64_t q = split_parent[k];
+                const lcs_pair &pr = pairs[q];
+                hn[k] = SweepNode{(int32_t)(3 * k), (int32_t)(3 * k + 1), (int32_t)(3 * k + 2), 0,
+                                  (int32_t)split_rm[k], (int32_t)pr.m};
+                hq[k] = SweepPair{pr.a, pr.b, pr.n, nullptr};
+                hpath[3 * k] = 0;                            // pathI[root] = 0
+                hpath[3 * n_split + 3 * k] = (int32_t)pr.n;  // pathJ[root] = n
+                SplitPair sp{};
+                sp.sub0 = desc(2 * k);
+                sp.sub1 = desc(2 * k + 1);
+                sp.b = pr.b;
+                sp.n = pr.n;
+                sp.lower = (int32_t)(3 * k + 2);
+                sp.big0 = half_desc[2 * k] < 0 ? 1 : 0;
+                sp.big1 = half_desc[2 * k + 1] < 0 ? 1 : 0;
+                sp.pathI = pathI;
+                sp.scratch = scr;
+                sp.len_out = t.d_lens + q;
+                sp.str = str_off[q] >= 0 ? t.d_strings + str_off[q] : nullptr;
+                sp.str1 = str_off[count + 2 * k + 1] >= 0 ? t.d_strings + str_off[count + 2 * k + 1] : nullptr;
+                sp.err = t.d_err;
+                hs[k] = sp;
+            }
+            SweepParams swp{};
+            swp.nodes = reinterpret_cast<const SweepNode *>(t.dev + o_snode);
+            swp.count = (int32_t)n_split;
+            swp.root_node = -1;
+            swp.n = split_nmax;
+            swp.pathI = pathI;
+            swp.pathJ = pathJ;
+            swp.fcnt = reinterpret_cast<int32_t *>(t.dev + o_fcnt);
+            swp.bcnt = reinterpret_cast<int32_t *>(t.dev + o_bcnt);
+            swp.err = t.d_err;
+            swp.pairs = reinterpret_cast<const SweepPair *>(t.dev + o_spair);
+            if (cudaMemcpyAsync(t.dev + o_split, hs.data(), sizeof(SplitPair) * n_split, cudaMemcpyHostToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(t.dev + o_snode, hn.data(), sizeof(SweepNode) * n_split, cudaMemcpyHostToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(t.dev + o_spair, hq.data(), sizeof(SweepPair) * n_split, cudaMemcpyHostToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(pathI, hpath.data(), sizeof(int32_t) * hpath.size(), cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess ||
+                launch_node_sweep(swp, split_rows, st) != cudaSuccess || launch_node_pick(swp, st) != cudaSuccess ||
+                launch_split_fix(reinterpret_cast<const SplitPair *>(t.dev + o_split), n_split, st) != cudaSuccess) {
+                s = fail(ctx, LCS_ECUDA, std::string("batch split pairs: ") + cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
         }
         // The classes run side by side, each on a stream forked from the
         // batch's; the tall pairs' kernels run on the batch's stream beside
@@ -2033,6 +2157,11 @@ lcs_status lcs_batch_submit(lcs_ctx *ctx, const lcs_pair *pairs, int64_t count, 
             if (joined[c] && cudaStreamWaitEvent(st, t.lane.ev_join[c], 0) != cudaSuccess && s == LCS_OK)
                 s = fail(ctx, LCS_ECUDA, "batch join");
         if (s != LCS_OK) break;
+        if (n_split > 0 &&
+            launch_split_join(reinterpret_cast<const SplitPair *>(t.dev + o_split), n_split, st) != cudaSuccess) {
+            s = fail(ctx, LCS_ECUDA, "batch split join");
+            break;
+        }
         // (The descriptor copies come from pageable host memory, which the
         // runtime stages before cudaMemcpyAsync returns.)
         if (cudaEventRecord(t.lane.ev_done, st) != cudaSuccess) s = fail(ctx, LCS_ECUDA, "batch event");

@@ -93,6 +93,29 @@ struct BatchParams {
     int *err;
     unsigned int *queue;   // work queue: the next position of `order` to take (zero at launch)
 };
+// A batch pair taller than one strip (up to two strips' rows) split at row
+// rm: the split column c comes from the recomputing sweeps (recompute.cu),
+// and its two halves (a[0:rm], b[0:c]) and (a[rm:m], b[c:n]) are ordinary
+// one-strip pairs of the batch.
+struct SplitPair {
+    BatchPair *sub0, *sub1;   // device descriptors of the halves (their b and n are set from c)
+    const uint8_t *b;
+    int64_t n;
+    int32_t lower;            // node id of the lower half: c = pathI[lower]
+    int32_t big0, big1;       // 1: the half runs on the tall kernels (cross vertices initialised here)
+    int32_t pad;
+    const int32_t *pathI;
+    uint32_t *scratch;        // the batch's scratch (tall halves' cross vertices)
+    int64_t *len_out;         // the pair's length: len0 + len1
+    uint8_t *str;             // the pair's string (the upper half's goes here), nullable
+    const uint8_t *str1;      // the lower half's string, appended after the upper's, nullable
+    int *err;
+};
+// Set the halves' columns (before the batch's kernels run).
+cudaError_t launch_split_fix(const SplitPair *sp, int64_t count, cudaStream_t st);
+// Join the halves' lengths and strings (after them).
+cudaError_t launch_split_join(const SplitPair *sp, int64_t count, cudaStream_t st);
+
 // The pairs of one words-per-lane class wpl (2, 4, 8 or 16: a up to
 // 1024 wpl rows) on one launch, a warp per pair.
 cudaError_t launch_batch_strip(const BatchParams &bp, int wpl, cudaStream_t st);
@@ -158,16 +181,23 @@ struct SweepNode {
     int32_t upper, lower;  // its children
     int32_t r0, rm, r1;    // rows: upper child [r0, rm), lower child [rm, r1)
 };
+// Strings of node q's pair when a launch covers nodes of several pairs.
+struct SweepPair {
+    const uint8_t *a, *b;
+    int64_t n;
+    int64_t *len_out;        // the node's maximum, nullable
+};
 struct SweepParams {
     const SweepNode *nodes;  // the nodes of one depth (device array)
     int32_t count;
     int32_t root_node;
     const uint8_t *a, *b;
-    int64_t n;
+    int64_t n;               // also the row stride of fcnt / bcnt (n + 1)
     int32_t *pathI, *pathJ;
     int32_t *fcnt, *bcnt;    // [count][n + 1] scratch: U(i, i + t), L(i + t, j)
     int64_t *len_out;        // the root's maximum (the LCS length), nullable
     int *err;
+    const SweepPair *pairs;  // nullable: node q's strings and length word are pairs[q]'s
 };
 int sweep_max_rows();
 cudaError_t launch_node_sweep(const SweepParams &p, int max_rows, cudaStream_t st);

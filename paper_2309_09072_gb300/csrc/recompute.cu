@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     const bool back = (blockIdx.x & 1) != 0;
     if (q >= p.count) return;
     const SweepNode nd = p.nodes[q];
-    const int64_t n = p.n;
+    const int64_t n = p.pairs ? p.pairs[q].n : p.n;
+    const uint8_t *A = p.pairs ? p.pairs[q].a : p.a, *Bs = p.pairs ? p.pairs[q].b : p.b;
     int64_t i = p.pathI[nd.node], j = p.pathJ[nd.node];
-    if (i < 0 || j > n || i > j) {                        // never for a consistent tree
+    if (i < 0 || j > n || i > j || n > p.n) {             // never for a consistent tree
         if (tid == 0) set_error(p.err, ERR_BOUNDS);
         i = j = 0;
     }
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
         if (tid == 0) set_error(p.err, ERR_BOUNDS);
         return;
     }
-    int32_t *cnt = (back ? p.bcnt : p.fcnt) + (int64_t)q * (n + 1);
+    int32_t *cnt = (back ? p.bcnt : p.fcnt) + (int64_t)q * (p.n + 1);
     const int64_t span = j - i;
     // Rows in sweep order (backward: reversed), and the letters present;
     // the columns' letters in sweep order (sb[c] for column c, 1-based,
@@ -86,10 +87,10 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     if (tid < 8) present[tid] = 0u;
     const bool staged_b = span <= C::kBCols;
     if (staged_b)
-        for (int c = tid; c < (int)span; c += blockDim.x) sb[c + 1] = back ? p.b[j - 1 - c] : p.b[i + c];
+        for (int c = tid; c < (int)span; c += blockDim.x) sb[c + 1] = back ? Bs[j - 1 - c] : Bs[i + c];
     __syncthreads();
     for (int r = tid; r < h; r += blockDim.x) {
-        const uint8_t ch = p.a[back ? r0 + h - 1 - r : r0 + r];
+        const uint8_t ch = A[back ? r0 + h - 1 - r : r0 + r];
         sa[r] = ch;
         atomicOr(&present[ch >> 5], 1u << (ch & 31));
     }
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     const int span32 = (int)span;
     auto letter_at = [&](int c) -> uint8_t {
         if (c < 1 || c > span32) return (uint8_t)0;
-        return staged_b ? sb[c] : (back ? p.b[j - c] : p.b[i + c - 1]);
+        return staged_b ? sb[c] : (back ? Bs[j - c] : Bs[i + c - 1]);
     };
     uint32_t V[WL];
 #pragma unroll
@@ -201,10 +202,10 @@ __global__ void __launch_bounds__(256) node_pick_kernel(SweepParams p) {
     __shared__ int64_t sk[8];
     const int q = blockIdx.x;
     const SweepNode nd = p.nodes[q];
-    const int64_t n = p.n;
+    const int64_t n = p.pairs ? p.pairs[q].n : p.n;
     int64_t i = p.pathI[nd.node], j = p.pathJ[nd.node];
-    if (i < 0 || j > n || i > j) i = j = 0;             // flagged by the sweep
-    const int32_t *f = p.fcnt + (int64_t)q * (n + 1), *g = p.bcnt + (int64_t)q * (n + 1);
+    if (i < 0 || j > n || i > j || n > p.n) i = j = 0;  // flagged by the sweep
+    const int32_t *f = p.fcnt + (int64_t)q * (p.n + 1), *g = p.bcnt + (int64_t)q * (p.n + 1);
     int best = INT32_MIN;
     int64_t bk = INT64_MAX;
     for (int64_t k = i + threadIdx.x; k <= j; k += blockDim.x) {
@@ -228,7 +229,11 @@ __global__ void __launch_bounds__(256) node_pick_kernel(SweepParams p) {
         p.pathJ[nd.upper] = c;
         p.pathI[nd.lower] = c;
         p.pathJ[nd.lower] = (int32_t)j;
-        if (nd.node == p.root_node && p.len_out) *p.len_out = best;
+        if (p.pairs) {
+            if (p.pairs[q].len_out) *p.pairs[q].len_out = best;
+        } else if (nd.node == p.root_node && p.len_out) {
+            *p.len_out = best;
+        }
     }
 }
 

@@ -172,3 +172,24 @@ def test_batch_admission_and_tickets():
         B.lcs_batch_release(c, t)
     finally:
         B.lcs_destroy(c)
+
+
+def test_batch_pairs_taller_than_one_strip(ctx):
+    """Pairs of 16385 to 32768 rows: the batch splits each at its middle row
+    by the recomputing sweeps (the split column is the smallest maximiser of
+    U(0, k) + L(k, n)), runs the two halves as one-strip pairs beside the
+    others, and joins their lengths and strings.  Every result must equal the
+    oracle's leftmost LCS, with and without strings, mixed with small pairs."""
+    rng = np.random.default_rng(2024)
+    pairs = []
+    for m, n, want in [(16385, 1500, True), (20001, 2000, True), (32768, 1200, True), (25000, 700, False),
+                       (17000, 1, True), (16500, 0, True)]:
+        pairs.append((inputs.uniform(rng, m, inputs.ACGT), inputs.uniform(rng, n, inputs.ACGT), want))
+    a = inputs.uniform(rng, 20000, inputs.ACGT)
+    pairs.append((a, inputs.mutate(rng, a[8000:11000], 0.10, 0.05, inputs.ACGT), True))   # split inside the match
+    a = inputs.uniform(rng, 18000, inputs.AA20)
+    pairs.append((a, inputs.mutate(rng, a[:2500], 0.10, 0.05, inputs.AA20), True))          # all in the upper half
+    for m, n in [(40, 90), (3000, 200), (5000, 4100)]:
+        pairs.append((inputs.uniform(rng, m, inputs.ACGT), inputs.uniform(rng, n, inputs.ACGT), True))
+    res, strings = run_batch(ctx, pairs)
+    check_exact(pairs, res, strings)
