@@ -788,6 +788,13 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
         }
     };
 
+    // First K-tile of a tile's top chunk: chunks of p.cap K-tiles aligned at
+    // the band's first K-tile.
+    auto top_chunk = [&](const DpxMeta &m) {
+        const int t0 = m.kl >> T_SHIFT;
+        return t0 + (((m.kh >> T_SHIFT) - t0) / p.cap) * p.cap;
+    };
+
     // Batches of tiles: with a counter, p.grab (1..32) consecutive tiles
     // taken from it (tile costs differ by orders of magnitude -- constant
     // tiles read nothing, wide bands stream several chunks -- so a static
@@ -878,8 +885,20 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = 0xC000C000u;
             // The band streams through shared memory p.cap K-tiles at a time
-            // (one chunk for almost every tile); accumulators persist.
-            for (int c0 = kt0; c0 <= ktop; c0 += p.cap) {
+            // (one chunk for most tiles), from its top chunk down, with the
+            // chunks aligned at kt0; accumulators persist.
+            //
+            // The band's low end: x, the largest maximiser of the corner
+            // (ia, ja) that is <= kh (kh is the smallest maximiser of the far
+            // corner).  For every entry (i, j) of the tile a maximiser below x
+            // can be replaced by x and one above kh by kh (Monge), so [x, kh]
+            // keeps a maximiser of every entry.  U's row ia and L's column ja
+            // are row 0 of the staged K-tiles: warp 0 searches each staged
+            // chunk that holds k <= ja from the top down for the largest k
+            // with U(ia, k) + L(k, ja) = D(ia, ja); the chunk that holds it is
+            // the last one the tile needs.
+            bool narrowed = !m.ok;             // corners that are not a DIST merge's: the whole band
+            for (int c0 = top_chunk(m);; c0 -= p.cap) {
                 const int c1 = min(ktop, c0 + p.cap - 1);
                 if (threadIdx.x == 0) {
                     if (!(st_tile == l && st_c0 == c0)) issue(m, c0);   // not prefetched
@@ -917,31 +936,29 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                     }
                 }
                 if (masked) __syncthreads();
-                if (m.ok && c0 == kt0 && c1 == ktop) {
-                    // The whole band is staged: narrow it to [x, kh], x the
-                    // largest maximiser of the corner (ia, ja) that is <= kh
-                    // (kh is the smallest maximiser of the far corner).  For
-                    // every entry (i, j) of the tile, a maximiser below x can
-                    // be replaced by x and one above kh by kh (Monge), so the
-                    // band keeps a maximiser of every entry.  U's row ia and
-                    // L's column ja are row 0 of the staged K-tiles.
+                if (!narrowed && c0 * T <= ja) {
                     if (threadIdx.x < 32) {
+                        const int top = min(min(m.kh, ja), c1 * T + T - 1), bot = max(m.kl, c0 * T);
                         int x = -1;
-                        for (int t = min(m.kh, ja); t >= m.kl && x < 0; t -= 32) {
+                        for (int t = top; t >= bot && x < 0; t -= 32) {
                             const int k = t - lane;
                             bool hit = false;
-                            if (k >= m.kl) {
+                            if (k >= bot) {
                                 const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
                                 hit = (int)Us[o] + (int)Ls[o] == m.va;
                             }
                             const unsigned bal = __ballot_sync(0xffffffffu, hit);
                             if (bal) x = t - (__ffs(bal) - 1);
                         }
-                        if (lane == 0) s_x = x < 0 ? m.kl : x;
+                        if (lane == 0) s_x = x;
                     }
                     __syncthreads();
-                    kbeg = s_x & ~3;
+                    if (s_x >= 0) {
+                        kbeg = s_x & ~3;
+                        narrowed = true;
+                    }
                 }
+                const bool last = narrowed || c0 == kt0;
                 for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
                     const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
                     const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
@@ -976,29 +993,30 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                         for (int b = 0; b < 4; ++b) lv[b] = ln[b];
                     }
                 }
-                if (threadIdx.x == 0 && c1 == ktop && store_pending) {
+                if (threadIdx.x == 0 && last && store_pending) {
                     bulk_wait_read0();          // the previous tile's store has read Ds
                     store_pending = false;
                 }
                 __syncthreads();                // the band is read; Ds is free
                 if (threadIdx.x == 0) {
-                    if (c1 < ktop) {
-                        issue(m, c1 + 1);       // next chunk of this tile
+                    if (!last) {
+                        issue(m, c0 - p.cap);   // next chunk of this tile, below
                         st_tile = l;
-                        st_c0 = c1 + 1;
+                        st_c0 = c0 - p.cap;
                     } else {
                         // Prefetch the next staged tile of the batch.
                         for (int l2 = l + 1; l2 < 32; ++l2) {
                             const DpxMeta m2 = s_meta[l2];
                             if (!m2.valid) break;
                             if (m2.cst) continue;
-                            issue(m2, m2.kl >> T_SHIFT);
+                            issue(m2, top_chunk(m2));
                             st_tile = l2;
-                            st_c0 = m2.kl >> T_SHIFT;
+                            st_c0 = top_chunk(m2);
                             break;
                         }
                     }
                 }
+                if (last) break;
             }
             const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
 #pragma unroll
