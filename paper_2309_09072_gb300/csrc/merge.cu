@@ -53,10 +53,10 @@ __device__ __forceinline__ void warp_argmax(int &v, int &k) {
 
 // ------------------------------------------------------------------ coarse
 int64_t coarse_sigma0(int64_t P) {
-    // Full scans on a sub-grid of about 17 x 17 points; each later level
+    // Full scans on a sub-grid of about 33 x 33 points; each later level
     // halves the stride down to 1.
     int64_t s = 1;
-    while (s * 16 < P) s <<= 1;
+    while (s * 32 < P) s <<= 1;
     return s;
 }
 
@@ -158,13 +158,72 @@ __global__ void __launch_bounds__(256) coarse_full_kernel(MergeParams p) {
     }
 }
 
+// One full-scan coarse point by a whole CTA, int16 operands: the leftmost
+// argmax of U(gi, k) + L(k, gj) over every k in [gi, gj].  A thread reads four
+// consecutive k of U's stored row gi and of L's stored column gj per 8-byte
+// load, then a block-wide (largest value, smallest k) reduction.  sv, sk: a
+// slot per warp.
+__device__ __forceinline__ void coarse_point_cta16(const MergeParams &p, int64_t sigma, int64_t w, int *sv,
+                                                   int *sk) {
+    const int64_t P = p.P, n = p.n;
+    const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);
+    const int64_t per_job = cnt * cnt;
+    const int job = (int)(w / per_job);
+    const int64_t rem = w - (int64_t)job * per_job;
+    const int64_t t = rem / cnt, u = rem - t * cnt;
+    const int64_t xp = min(t * sigma, P), xq = min(u * sigma, P);
+    if (xp > xq) return;                          // the same for the whole CTA
+    const MergeJob jb = p.jobs[job];
+    const int16_t *U = reinterpret_cast<const int16_t *>(jb.U);
+    const int16_t *L = reinterpret_cast<const int16_t *>(jb.L);
+    const int gi = (int)grid_vertex_s(xp, n, p.gshift), gj = (int)grid_vertex_s(xq, n, p.gshift);
+    const int64_t Ib = gi >> T_SHIFT, Jb = gj >> T_SHIFT;
+    constexpr int PI = Fmt<int16_t>::P;
+    constexpr int64_t EI = Fmt<int16_t>::ELEMS;
+    const int ro = (gi & (T - 1)) * PI, co = (gj & (T - 1)) * PI;
+    int best = INT32_MIN, bk = INT32_MAX;
+#pragma unroll 2
+    for (int kb = (gi & ~3) + 4 * (int)threadIdx.x; kb <= gj; kb += 4 * (int)blockDim.x) {
+        const int64_t kt = kb >> T_SHIFT;
+        const int o = kb & (T - 1);
+        const uint2 uu = *reinterpret_cast<const uint2 *>(U + row_tile(Ib, kt, p.NT) * EI + ro + o);
+        const uint2 ll = *reinterpret_cast<const uint2 *>(L + col_tile(kt, Jb) * EI + co + o);
+        const uint32_t uw[2] = {uu.x, uu.y}, lw[2] = {ll.x, ll.y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = kb + e;
+            const int v = (int)(int16_t)(uw[e >> 1] >> (16 * (e & 1))) + (int)(int16_t)(lw[e >> 1] >> (16 * (e & 1)));
+            if (k >= gi && k <= gj && v > best) { best = v; bk = k; }   // k increases: first max per thread
+        }
+    }
+    warp_argmax(best, bk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            if (sv[q] > best || (sv[q] == best && sk[q] < bk)) { best = sv[q]; bk = sk[q]; }
+        if (bk == INT32_MAX) { set_error(p.err, ERR_BOUNDS); bk = gi; best = 0; }
+        jb.kgrid[xp * (P + 1) + xq] = bk;
+        jb.vgrid[xp * (P + 1) + xq] = best;
+    }
+    __syncthreads();                              // sv, sk free again
+}
+
+// The full-scan level for int16 operands: a CTA per point, four k per load.
+__global__ void __launch_bounds__(256) coarse_full16_kernel(MergeParams p) {
+    pdl_wait_and_release();
+    __shared__ int sv[8], sk[8];
+    coarse_point_cta16(p, p.sigma, (int64_t)blockIdx.x, sv, sk);
+}
+
 cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
     if (p.full) {
         const int64_t cnt = p.P / p.sigma + 1 + ((p.P % p.sigma) ? 1 : 0);
         const unsigned blocks = (unsigned)(cnt * cnt * p.njobs);
         switch (in_dtype) {
             case DT_U8: return launch_pdl(coarse_full_kernel<uint8_t>, dim3(blocks), dim3(256), 0, st, p);
-            case DT_I16: return launch_pdl(coarse_full_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, p);
+            case DT_I16: return launch_pdl(coarse_full16_kernel, dim3(blocks), dim3(256), 0, st, p);
             case DT_I32: return launch_pdl(coarse_full_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, p);
             default: return cudaErrorInvalidValue;
         }
