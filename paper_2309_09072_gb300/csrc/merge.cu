@@ -753,11 +753,15 @@ constexpr int16_t kNegInf16 = -16384;
 struct DpxSmem {
     size_t ds, us, ls, total;
 };
-__host__ __device__ inline DpxSmem dpx_smem_layout(int out_dt, int cap) {
+// The output tile is staged in shared memory only for a launch that writes
+// the caller's dense matrix (`dense`); packed tiles go from registers to
+// global memory.
+__host__ __device__ inline DpxSmem dpx_smem_layout(int out_dt, int cap, bool dense) {
     DpxSmem s;
     const size_t tileb = (size_t)T * tile_pitch(DT_I16) * 2;   // 8704
     size_t off = 16;
-    s.ds = off; off = align16c(off + (size_t)T * tile_pitch(out_dt) * dt_bytes(out_dt));
+    s.ds = off;
+    if (dense) off = align16c(off + (size_t)T * tile_pitch(out_dt) * dt_bytes(out_dt));
     s.us = off; off = align16c(off + (size_t)cap * tileb);
     s.ls = off; off = align16c(off + (size_t)cap * tileb);
     s.total = off;
@@ -810,7 +814,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     constexpr int EI = Fmt<TIn>::ELEMS, EO = Fmt<TOut>::ELEMS;
     constexpr uint32_t tileB = (uint32_t)(EI * sizeof(TIn));
     extern __shared__ __align__(128) unsigned char smem[];
-    const DpxSmem SL = dpx_smem_layout(DtOf<TOut>::v, p.cap);
+    const DpxSmem SL = dpx_smem_layout(DtOf<TOut>::v, p.cap, p.dense_out != nullptr);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
@@ -834,7 +838,6 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     // loading) and the barrier parity to wait for.
     int st_tile = -1, st_c0 = -1;             // batch slot and first K-tile staged
     uint32_t phase = 0;
-    bool store_pending = false;
     auto issue = [&](const DpxMeta &m, int c0) {
         const int c1 = min(m.kh >> T_SHIFT, c0 + p.cap - 1);
         const MergeJob jb = p.jobs[m.job];
@@ -917,6 +920,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
             if (!m.valid) break;
             const MergeJob jb = p.jobs[m.job];
             const int layout = jb.d_layout;
+            const bool col_out = layout == LAYOUT_COL;
             const int ia = m.I * T, ja = m.J * T;
             if (m.cst) {
                 // Constant tile: written here, nothing staged.
@@ -1020,24 +1024,31 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 const bool last = narrowed || c0 == kt0;
                 for (int kt = max(c0, kbeg >> T_SHIFT); kt <= min(c1, kend >> T_SHIFT); ++kt) {
                     const int lo = max(kbeg, kt * T) & (T - 1), hi = min(kend, kt * T + T - 1) & (T - 1);
-                    const TIn *Ub = Us + (kt - c0) * EI + ty * PI;
-                    const TIn *Lb = Ls + (kt - c0) * EI + tx * PI;
+                    // Thread (tx, ty) owns the 8 x 4 entries at stored-tile
+                    // rows ty + 8a and columns tx + 16b of the output image:
+                    // D rows x of U's rows and D columns y of L's stored rows
+                    // in row (and dense) layout, transposed in column layout,
+                    // so that the 16 lanes of a half-warp store consecutive
+                    // elements either way.  (max,+) is symmetric in its two
+                    // operands, so only the roles of the staged tiles swap.
+                    const TIn *Ab = (col_out ? Ls : Us) + (kt - c0) * EI + ty * PI;
+                    const TIn *Bb = (col_out ? Us : Ls) + (kt - c0) * EI + tx * PI;
                     // Four k per step; the next step's operands load while
                     // this step computes, and the two k pairs of a step go
                     // through all 32 accumulators in turn, so that dependent
                     // DPX instructions are 32 apart.
                     uint2 u[8], lv[4];
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + lo);
+                    for (int a = 0; a < 8; ++a) u[a] = *reinterpret_cast<const uint2 *>(Ab + a * 8 * PI + lo);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) lv[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + lo);
+                    for (int b = 0; b < 4; ++b) lv[b] = *reinterpret_cast<const uint2 *>(Bb + b * 16 * PI + lo);
                     for (int kk = lo; kk <= hi; kk += 4) {
                         const int kn = kk + 4 <= hi ? kk + 4 : kk;   // stays inside the staged tile
                         uint2 un[8], ln[4];
 #pragma unroll
-                        for (int a = 0; a < 8; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ub + a * 8 * PI + kn);
+                        for (int a = 0; a < 8; ++a) un[a] = *reinterpret_cast<const uint2 *>(Ab + a * 8 * PI + kn);
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Lb + b * 16 * PI + kn);
+                        for (int b = 0; b < 4; ++b) ln[b] = *reinterpret_cast<const uint2 *>(Bb + b * 16 * PI + kn);
 #pragma unroll
                         for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -1052,11 +1063,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                         for (int b = 0; b < 4; ++b) lv[b] = ln[b];
                     }
                 }
-                if (threadIdx.x == 0 && last && store_pending) {
-                    bulk_wait_read0();          // the previous tile's store has read Ds
-                    store_pending = false;
-                }
-                __syncthreads();                // the band is read; Ds is free
+                __syncthreads();                // the band is read
                 if (threadIdx.x == 0) {
                     if (!last) {
                         issue(m, c0 - p.cap);   // next chunk of this tile, below
@@ -1077,28 +1084,34 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 }
                 if (last) break;
             }
-            const int ds_sx = layout == LAYOUT_COL ? 1 : PO, ds_sy = layout == LAYOUT_COL ? PO : 1;
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int x = ty + 8 * a, y = tx + 16 * b;
-                    const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
-                    Ds[x * ds_sx + y * ds_sy] = (TOut)v;
-                }
-            if (layout != LAYOUT_DENSE) fence_proxy_async_smem();
-            __syncthreads();
             if (layout == LAYOUT_DENSE) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+                        Ds[(ty + 8 * a) * PO + tx + 16 * b] = (TOut)v;
+                    }
+                __syncthreads();
                 store_dense_tile<TOut>(reinterpret_cast<TOut *>(p.dense_out), p.ld, ia, ja, min(T, n + 1 - ia),
                                        min(T, n + 1 - ja), [&](int x, int y) {
                                            return ia + x > ja + y ? Sentinel<TOut>::value : Ds[x * PO + y];
                                        });
                 __syncthreads();                // Ds read before the next tile writes it
-            } else if (threadIdx.x == 0) {
-                const int64_t tile = (layout == LAYOUT_COL) ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
-                bulk_s2g(reinterpret_cast<TOut *>(jb.D) + tile * EO, Ds, (uint32_t)(EO * sizeof(TOut)));
-                bulk_commit();
-                store_pending = true;
+            } else {
+                // The tile image straight from the accumulators: entry
+                // (ty + 8a, tx + 16b) of the stored tile (rows past n and
+                // below the diagonal carry unspecified values, as in every
+                // stored tile).
+                const int64_t tile = col_out ? col_tile(m.I, m.J) : row_tile(m.I, m.J, NT);
+                TOut *dt = reinterpret_cast<TOut *>(jb.D) + tile * EO + ty * PO + tx;
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int v = max((int)(int16_t)(acc[a][b] & 0xFFFFu), (int)(int16_t)(acc[a][b] >> 16));
+                        dt[a * 8 * PO + b * 16] = (TOut)v;
+                    }
             }
         }
     }
@@ -1112,7 +1125,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
 
 template <typename TOut>
 static cudaError_t launch_dpx_t(const MergeParams &p, cudaStream_t st) {
-    const size_t smem = dpx_smem_layout(DtOf<TOut>::v, p.cap).total;
+    const size_t smem = dpx_smem_layout(DtOf<TOut>::v, p.cap, p.dense_out != nullptr).total;
     auto kern = tile_dpx_kernel<TOut>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
