@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
     TOut *Ds = reinterpret_cast<TOut *>(smem + SL.ds);
     TIn *Us = reinterpret_cast<TIn *>(smem + SL.us);
     TIn *Ls = reinterpret_cast<TIn *>(smem + SL.ls);
-    __shared__ int s_ok, s_x;
+    __shared__ int s_ok;
     __shared__ DpxMeta s_meta[32];
     __shared__ int64_t s_grab;
 
@@ -1000,24 +1000,22 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                 }
                 if (masked) __syncthreads();
                 if (!narrowed && c0 * T <= ja) {
-                    if (threadIdx.x < 32) {
-                        const int top = min(min(m.kh, ja), c1 * T + T - 1), bot = max(m.kl, c0 * T);
-                        int x = -1;
-                        for (int t = top; t >= bot && x < 0; t -= 32) {
-                            const int k = t - lane;
-                            bool hit = false;
-                            if (k >= bot) {
-                                const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
-                                hit = (int)Us[o] + (int)Ls[o] == m.va;
-                            }
-                            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                            if (bal) x = t - (__ffs(bal) - 1);
+                    // Every warp runs the same search on the same staged
+                    // data (a ballot or two), so no barrier hands x over.
+                    const int top = min(min(m.kh, ja), c1 * T + T - 1), bot = max(m.kl, c0 * T);
+                    int x = -1;
+                    for (int t = top; t >= bot && x < 0; t -= 32) {
+                        const int k = t - lane;
+                        bool hit = false;
+                        if (k >= bot) {
+                            const int o = ((k >> T_SHIFT) - c0) * EI + (k & (T - 1));
+                            hit = (int)Us[o] + (int)Ls[o] == m.va;
                         }
-                        if (lane == 0) s_x = x;
+                        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                        if (bal) x = t - (__ffs(bal) - 1);
                     }
-                    __syncthreads();
-                    if (s_x >= 0) {
-                        kbeg = s_x & ~3;
+                    if (x >= 0) {
+                        kbeg = x & ~3;
                         narrowed = true;
                     }
                 }
