@@ -254,6 +254,68 @@ template <> struct AddChain<8> {
     }
 };
 
+template <> struct AddChain<3> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[3], const uint32_t (&x)[3],
+                                                   const uint32_t (&y)[3]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %4, %7;\n\t"
+            "addc.cc.u32 %1, %5, %8;\n\t"
+            "addc.cc.u32 %2, %6, %9;\n\t"
+            "addc.u32 %3, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(y[0]), "r"(y[1]), "r"(y[2]));
+        return c;
+    }
+};
+template <> struct AddChain<5> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[5], const uint32_t (&x)[5],
+                                                   const uint32_t (&y)[5]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %6, %11;\n\t"
+            "addc.cc.u32 %1, %7, %12;\n\t"
+            "addc.cc.u32 %2, %8, %13;\n\t"
+            "addc.cc.u32 %3, %9, %14;\n\t"
+            "addc.cc.u32 %4, %10, %15;\n\t"
+            "addc.u32 %5, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]));
+        return c;
+    }
+};
+template <> struct AddChain<6> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[6], const uint32_t (&x)[6],
+                                                   const uint32_t (&y)[6]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %7, %13;\n\t"
+            "addc.cc.u32 %1, %8, %14;\n\t"
+            "addc.cc.u32 %2, %9, %15;\n\t"
+            "addc.cc.u32 %3, %10, %16;\n\t"
+            "addc.cc.u32 %4, %11, %17;\n\t"
+            "addc.cc.u32 %5, %12, %18;\n\t"
+            "addc.u32 %6, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]));
+        return c;
+    }
+};
+template <> struct AddChain<7> {
+    static __device__ __forceinline__ uint32_t run(uint32_t (&s)[7], const uint32_t (&x)[7],
+                                                   const uint32_t (&y)[7]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %8, %15;\n\t"
+            "addc.cc.u32 %1, %9, %16;\n\t"
+            "addc.cc.u32 %2, %10, %17;\n\t"
+            "addc.cc.u32 %3, %11, %18;\n\t"
+            "addc.cc.u32 %4, %12, %19;\n\t"
+            "addc.cc.u32 %5, %13, %20;\n\t"
+            "addc.cc.u32 %6, %14, %21;\n\t"
+            "addc.u32 %7, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(c)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]));
+        return c;
+    }
+};
+
 // One bit-vector column step (u = V & M, V' = (V + u) | (V & ~M), the
 // Allison-Dix / Hyyro step restated) for one source; returns the carry out
 // of the top row, the increment of DIST.
@@ -266,6 +328,28 @@ __device__ __forceinline__ uint32_t column_step(uint32_t (&V)[W], const uint32_t
 #pragma unroll
     for (int w = 0; w < W; ++w) V[w] = s[w] | (V[w] & ~M[w]);
     return c;
+}
+
+// The same step over words [S, W) only, for a vector whose words below S are
+// zero: a zero word gives no carry and stays zero (u = 0, V + 0 = 0), so the
+// chain starts at word S with no carry in.  The carry out is the same.
+template <int W, int S>
+__device__ __forceinline__ uint32_t column_step_tail(uint32_t (&V)[W], const uint32_t (&M)[W]) {
+    constexpr int N = W - S;
+    if constexpr (N <= 0) {
+        return 0u;
+    } else {
+        uint32_t x[N], u[N], s[N];
+#pragma unroll
+        for (int w = 0; w < N; ++w) {
+            x[w] = V[S + w];
+            u[w] = x[w] & M[S + w];
+        }
+        const uint32_t c = AddChain<N>::run(s, x, u);
+#pragma unroll
+        for (int w = 0; w < N; ++w) V[S + w] = s[w] | (x[w] & ~M[S + w]);
+        return c;
+    }
 }
 
 // ------------------------------------------------------------------ multi-word adds with carry in

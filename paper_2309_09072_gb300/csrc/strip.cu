@@ -64,6 +64,18 @@ __device__ __forceinline__ void write_tile_part(const StripParams &p, OutT *out,
     }
 }
 
+// Calls f(std::integral_constant<int, w0>{}) for a run-time w0 in [0, W].
+template <int W, int K = 0, typename F>
+__device__ __forceinline__ void dispatch_start(int w0, F &&f) {
+    if constexpr (K <= W) {
+        if (w0 == K) {
+            f(std::integral_constant<int, K>{});
+            return;
+        }
+        dispatch_start<W, K + 1>(w0, f);
+    }
+}
+
 template <typename OutT, int W>
 __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) {
     pdl_wait_and_release();
@@ -118,6 +130,11 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
         return (Jt < p.NT && j >= 1 && j <= n) ? (int)p.b[j - 1] : -1;
     };
     int ch_next = letter(I);
+    // Rows are matched from the top of the strip down: once the first 32 w
+    // rows of a source have all stepped (its low words are zero), they stay
+    // so, and the column step runs from word w on (column_step_tail).  w0 is
+    // the warp's smallest such w, refreshed after every tile.
+    int w0 = 0;
     for (int64_t J = I; J < p.NT; ++J) {
         const int64_t jb = J * T;
         // Column masks of this tile (each warp of the pair builds half).
@@ -144,26 +161,39 @@ __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) 
             }
         } else {
             // Column c + 1's masks load while column c's carry chain runs;
-            // the staging stride is a constant of each layout's loop.
-            auto sweep = [&](auto col_layout) {
+            // the staging stride is a constant of each layout's loop, and
+            // the first live word S of the warp's vectors is a constant of
+            // each instantiation.
+            auto sweep = [&](auto col_layout, auto start) {
                 constexpr int SC = decltype(col_layout)::value ? P : 1, SR = decltype(col_layout)::value ? 1 : P;
-                uint32_t Mn[W];
+                constexpr int S = decltype(start)::value;
+                uint32_t Mn[W] = {};
 #pragma unroll
-                for (int w = 0; w < W; ++w) Mn[w] = colm[w];
+                for (int w = S; w < W; ++w) Mn[w] = colm[w];
 #pragma unroll 4
                 for (int c = 0; c < cmax; ++c) {
-                    uint32_t M[W];
+                    uint32_t M[W] = {};
 #pragma unroll
-                    for (int w = 0; w < W; ++w) M[w] = Mn[w];
+                    for (int w = S; w < W; ++w) M[w] = Mn[w];
                     const int cn = c + 1 < cmax ? c + 1 : c;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) Mn[w] = colm[cn * W + w];
-                    d += (int)column_step<W>(V, M);
+                    for (int w = S; w < W; ++w) Mn[w] = colm[cn * W + w];
+                    d += (int)column_step_tail<W, S>(V, M);
                     stage[c * SC + r * SR] = (OutT)d;
                 }
             };
-            if (layout == LAYOUT_COL) sweep(std::true_type{});
-            else sweep(std::false_type{});
+            dispatch_start<W>(w0, [&](auto start) {
+                if (layout == LAYOUT_COL) sweep(std::true_type{}, start);
+                else sweep(std::false_type{}, start);
+            });
+        }
+        {
+            int z = W;
+#pragma unroll
+            for (int w = W - 1; w >= 0; --w)
+                if (V[w] != 0u) z = w;
+            if (i0 + r > n) z = W;             // no source in this lane
+            w0 = __reduce_min_sync(0xFFFFFFFFu, z);
         }
         // Once every source of the band has matched all hs rows, DIST stays
         // hs for the rest of the row: the remaining tiles are constant.
