@@ -426,6 +426,9 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         t.L = reinterpret_cast<const void *>(P.nodes[mg.l].off);
         t.in_dtype = mg.in_dt;
         t.node = mg.out; t.upper = mg.u; t.lower = mg.l;
+        // The root's grid is computed beside the traceback (the root merge
+        // group runs on a side stream): the root level scans its whole row.
+        t.kgrid = (mg.out == P.root) ? nullptr : reinterpret_cast<const int32_t *>(mg.kgrid_off);
         P.h_tb[q] = t;
     }
     P.h_jobs.resize(P.merges.size());
@@ -817,6 +820,7 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb
         for (auto &t : tb) {
             t.U = reloc(base, (const char *)t.U);
             t.L = reloc(base, (const char *)t.L);
+            if (t.kgrid) t.kgrid = reloc(base, t.kgrid);
         }
         LCS_CK(ctx, cudaMemcpy(base + Q.off_strip_outs, so.data(), sizeof(StripOut) * so.size(),
                                cudaMemcpyHostToDevice));

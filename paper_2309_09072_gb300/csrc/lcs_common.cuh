@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include <cuda_runtime.h>
@@ -349,6 +350,18 @@ __device__ __forceinline__ uint32_t column_step_tail(uint32_t (&V)[W], const uin
 #pragma unroll
         for (int w = 0; w < N; ++w) V[S + w] = s[w] | (x[w] & ~M[S + w]);
         return c;
+    }
+}
+
+// Calls f(std::integral_constant<int, w0>{}) for a run-time w0 in [0, W].
+template <int W, int K = 0, typename F>
+__device__ __forceinline__ void dispatch_start(int w0, F &&f) {
+    if constexpr (K <= W) {
+        if (w0 == K) {
+            f(std::integral_constant<int, K>{});
+            return;
+        }
+        dispatch_start<W, K + 1>(w0, f);
     }
 }
 

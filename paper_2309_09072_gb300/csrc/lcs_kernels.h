@@ -150,6 +150,7 @@ cudaError_t launch_fill_lower(void *out, int dtype, int64_t n, int64_t ld, int l
 struct TbMerge {
     const void *U;        // upper child (row layout)
     const void *L;        // lower child (column layout)
+    const int32_t *kgrid; // the merge's argmax on the T-grid (complete when the level runs), or null
     int32_t in_dtype;
     int32_t node;         // index of the merged node (its path endpoints)
     int32_t upper;        // child node indices

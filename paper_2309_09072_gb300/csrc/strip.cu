@@ -64,18 +64,6 @@ __device__ __forceinline__ void write_tile_part(const StripParams &p, OutT *out,
     }
 }
 
-// Calls f(std::integral_constant<int, w0>{}) for a run-time w0 in [0, W].
-template <int W, int K = 0, typename F>
-__device__ __forceinline__ void dispatch_start(int w0, F &&f) {
-    if constexpr (K <= W) {
-        if (w0 == K) {
-            f(std::integral_constant<int, K>{});
-            return;
-        }
-        dispatch_start<W, K + 1>(w0, f);
-    }
-}
-
 template <typename OutT, int W>
 __global__ void __launch_bounds__(kStripWarps * 32) strip_kernel(StripParams p) {
     pdl_wait_and_release();

@@ -30,9 +30,24 @@ __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
         i = 0;
         j = 0;
     }
+    // The leftmost argmax is monotone in both coordinates (Monge), so with the
+    // merge's argmax grid it lies between the grid's values at the tile
+    // corners around (i, j).
+    int64_t lo = i, hi = j;
+    if (mg.kgrid) {
+        const int64_t P = (p.n + T - 1) >> T_SHIFT;
+        const int64_t I0 = min(i >> T_SHIFT, P), J0 = min(j >> T_SHIFT, P);
+        const int64_t I1 = min(I0 + 1, P), J1 = min(J0 + 1, P);
+        lo = max(lo, (int64_t)mg.kgrid[I0 * (P + 1) + J0]);
+        hi = min(hi, (int64_t)mg.kgrid[I1 * (P + 1) + J1]);
+        if (lo > hi) {                       // not a DIST merge's grid: the whole row
+            lo = i;
+            hi = j;
+        }
+    }
     int best = INT32_MIN;
     int64_t bk = INT64_MAX;
-    for (int64_t k = i + threadIdx.x; k <= j; k += blockDim.x) {
+    for (int64_t k = lo + threadIdx.x; k <= hi; k += blockDim.x) {
         const int v = load_row_any(mg.U, i, k, p.NT, mg.in_dtype) + load_col_any(mg.L, k, j, mg.in_dtype);
         if (v > best) { best = v; bk = k; }
     }
@@ -159,16 +174,31 @@ __device__ __forceinline__ void leaf_sweep(const uint32_t *masks, const uint8_t 
         for (int w = 0; w < W; ++w) M[w] = m0[w];
         chn = letter(ncol > 1 ? 2 : 1);
     }
-    for (int c = 1; c <= ncol; ++c) {
-        uint32_t Mn[W];
-        const uint32_t *mn = masks + chn * W;
+    // Blocks of 32 columns; the vector's settled low words (zero, carrying
+    // nothing: rows are matched from the first row down) are skipped by the
+    // add-with-carry chain, the start word refreshed after every block.
+    int w0 = 0;
+    for (int c = 1; c <= ncol;) {
+        const int cend = min(ncol, c + 31);
+        dispatch_start<W>(w0, [&](auto start) {
+            constexpr int S = decltype(start)::value;
+            for (; c <= cend; ++c) {
+                uint32_t Mn[W];
+                const uint32_t *mn = masks + chn * W;
 #pragma unroll
-        for (int w = 0; w < W; ++w) Mn[w] = mn[w];
-        chn = letter(c + 2 <= ncol ? c + 2 : ncol);
-        column_step<W>(V, M);
-        if (lane == 0) store_words<W>(out + c * W, V);
+                for (int w = 0; w < W; ++w) Mn[w] = mn[w];
+                chn = letter(c + 2 <= ncol ? c + 2 : ncol);
+                column_step_tail<W, S>(V, M);
+                if (lane == 0) store_words<W>(out + c * W, V);
 #pragma unroll
-        for (int w = 0; w < W; ++w) M[w] = Mn[w];
+                for (int w = 0; w < W; ++w) M[w] = Mn[w];
+            }
+        });
+        int z = W;
+#pragma unroll
+        for (int w = W - 1; w >= 0; --w)
+            if (V[w] != 0u) z = w;
+        w0 = z;
     }
 }
 
