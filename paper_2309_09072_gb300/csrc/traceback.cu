@@ -174,31 +174,16 @@ __device__ __forceinline__ void leaf_sweep(const uint32_t *masks, const uint8_t 
         for (int w = 0; w < W; ++w) M[w] = m0[w];
         chn = letter(ncol > 1 ? 2 : 1);
     }
-    // Blocks of 32 columns; the vector's settled low words (zero, carrying
-    // nothing: rows are matched from the first row down) are skipped by the
-    // add-with-carry chain, the start word refreshed after every block.
-    int w0 = 0;
-    for (int c = 1; c <= ncol;) {
-        const int cend = min(ncol, c + 31);
-        dispatch_start<W>(w0, [&](auto start) {
-            constexpr int S = decltype(start)::value;
-            for (; c <= cend; ++c) {
-                uint32_t Mn[W];
-                const uint32_t *mn = masks + chn * W;
+    for (int c = 1; c <= ncol; ++c) {
+        uint32_t Mn[W];
+        const uint32_t *mn = masks + chn * W;
 #pragma unroll
-                for (int w = 0; w < W; ++w) Mn[w] = mn[w];
-                chn = letter(c + 2 <= ncol ? c + 2 : ncol);
-                column_step_tail<W, S>(V, M);
-                if (lane == 0) store_words<W>(out + c * W, V);
+        for (int w = 0; w < W; ++w) Mn[w] = mn[w];
+        chn = letter(c + 2 <= ncol ? c + 2 : ncol);
+        column_step<W>(V, M);
+        if (lane == 0) store_words<W>(out + c * W, V);
 #pragma unroll
-                for (int w = 0; w < W; ++w) M[w] = Mn[w];
-            }
-        });
-        int z = W;
-#pragma unroll
-        for (int w = W - 1; w >= 0; --w)
-            if (V[w] != 0u) z = w;
-        w0 = z;
+        for (int w = 0; w < W; ++w) M[w] = Mn[w];
     }
 }
 
