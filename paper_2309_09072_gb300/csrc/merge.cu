@@ -41,6 +41,19 @@ __device__ __forceinline__ int64_t grid_vertex_s(int64_t p, int64_t n, int gshif
     return min(p << (gshift ? gshift : T_SHIFT), n);
 }
 
+// Point rem of the upper triangle t <= u of a cnt x cnt grid, row by row:
+// row t starts at t cnt - t (t - 1) / 2.
+__device__ __forceinline__ void tri_point(int64_t rem, int64_t cnt, int64_t &t, int64_t &u) {
+    auto start = [&](int64_t x) { return x * cnt - x * (x - 1) / 2; };
+    const float b = 2.0f * (float)cnt + 1.0f;
+    int64_t r = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)rem, 0.0f))) * 0.5f);
+    r = max((int64_t)0, min(r, cnt - 1));
+    while (r + 1 < cnt && start(r + 1) <= rem) ++r;
+    while (r > 0 && start(r) > rem) --r;
+    t = r;
+    u = r + (rem - start(r));
+}
+
 // Warp-wide (value, k) reduction: largest value, smallest k among equals.
 __device__ __forceinline__ void warp_argmax(int &v, int &k) {
 #pragma unroll
@@ -65,15 +78,15 @@ __global__ void __launch_bounds__(256) coarse_kernel(MergeParams p) {
     pdl_wait_and_release();
     const int64_t P = p.P, n = p.n, sigma = p.sigma;
     const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);   // points 0, s, 2s, .., P
-    const int64_t per_job = cnt * cnt;
+    const int64_t per_job = cnt * (cnt + 1) / 2;                  // t <= u
     const int64_t total = per_job * p.njobs;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = warp0; w < total; w += nwarps) {
         const int job = (int)(w / per_job);
-        const int64_t rem = w - (int64_t)job * per_job;
-        const int64_t t = rem / cnt, u = rem - t * cnt;
+        int64_t t, u;
+        tri_point(w - (int64_t)job * per_job, cnt, t, u);
         const int64_t xp = min(t * sigma, P), xq = min(u * sigma, P);
         if (xp > xq) continue;
         const bool newp = (t & 1) && xp < P;
@@ -129,10 +142,10 @@ __global__ void __launch_bounds__(256) coarse_full_kernel(MergeParams p) {
     __shared__ int sv[8], sk[8];
     const int64_t P = p.P, n = p.n, sigma = p.sigma;
     const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);
-    const int64_t per_job = cnt * cnt;
+    const int64_t per_job = cnt * (cnt + 1) / 2;                  // t <= u
     const int job = (int)(blockIdx.x / per_job);
-    const int64_t rem = blockIdx.x - (int64_t)job * per_job;
-    const int64_t t = rem / cnt, u = rem - t * cnt;
+    int64_t t, u;
+    tri_point(blockIdx.x - (int64_t)job * per_job, cnt, t, u);
     const int64_t xp = min(t * sigma, P), xq = min(u * sigma, P);
     if (xp > xq) return;
     const MergeJob jb = p.jobs[job];
@@ -167,10 +180,10 @@ __device__ __forceinline__ void coarse_point_cta16(const MergeParams &p, int64_t
                                                    int *sk) {
     const int64_t P = p.P, n = p.n;
     const int64_t cnt = P / sigma + 1 + ((P % sigma) ? 1 : 0);
-    const int64_t per_job = cnt * cnt;
+    const int64_t per_job = cnt * (cnt + 1) / 2;                  // t <= u
     const int job = (int)(w / per_job);
-    const int64_t rem = w - (int64_t)job * per_job;
-    const int64_t t = rem / cnt, u = rem - t * cnt;
+    int64_t t, u;
+    tri_point(w - (int64_t)job * per_job, cnt, t, u);
     const int64_t xp = min(t * sigma, P), xq = min(u * sigma, P);
     if (xp > xq) return;                          // the same for the whole CTA
     const MergeJob jb = p.jobs[job];
@@ -220,7 +233,7 @@ __global__ void __launch_bounds__(256) coarse_full16_kernel(MergeParams p) {
 cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
     if (p.full) {
         const int64_t cnt = p.P / p.sigma + 1 + ((p.P % p.sigma) ? 1 : 0);
-        const unsigned blocks = (unsigned)(cnt * cnt * p.njobs);
+        const unsigned blocks = (unsigned)(cnt * (cnt + 1) / 2 * p.njobs);
         switch (in_dtype) {
             case DT_U8: return launch_pdl(coarse_full_kernel<uint8_t>, dim3(blocks), dim3(256), 0, st, p);
             case DT_I16: return launch_pdl(coarse_full16_kernel, dim3(blocks), dim3(256), 0, st, p);
@@ -228,8 +241,8 @@ cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
             default: return cudaErrorInvalidValue;
         }
     }
-    const int64_t cnt = p.P / p.sigma + 2;
-    const int64_t warps = cnt * cnt * p.njobs;
+    const int64_t cnt = p.P / p.sigma + 1 + ((p.P % p.sigma) ? 1 : 0);
+    const int64_t warps = cnt * (cnt + 1) / 2 * p.njobs;
     int64_t blocks = ceil_div(warps, 8);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
