@@ -27,6 +27,12 @@
 //      plain stores for a dense matrix.
 //      Tiles whose k-window exceeds the shared-memory band fall back to the
 //      same refinement reading global memory.
+//   3. tile_dpx_kernel (int16 operands, D only): persistent CTAs take tiles
+//      from a counter; a tile's band [kl, kh] (narrowed at its low end to the
+//      largest maximiser of the near corner that is <= kh) streams through
+//      shared memory from its top chunk down, and the band's (max,+) product
+//      runs on DPX; packed output tiles go from the accumulators to global
+//      memory, the root's dense tile through shared memory.
 #include <algorithm>
 
 #include "lcs_common.cuh"
@@ -984,8 +990,8 @@ __global__ void __launch_bounds__(kDpxThreads) tile_dpx_kernel(MergeParams p) {
                         set_error(p.err, ERR_TIMEOUT);
                         s_ok = 0;
                         // Before the early return: copies that are only late
-                        // land (a second bounded wait) and the previous
-                        // tile's bulk store has read its shared memory.
+                        // land (a second bounded wait), and no bulk copy of
+                        // this CTA is left in flight.
                         mbar_wait_bounded(bar, phase, lim);
                         bulk_wait_all0();
                     }
