@@ -50,7 +50,7 @@ struct RcCfg {
     static constexpr size_t bytes = o_b + kBCols + 64;
 };
 
-template <int NW>
+template <int NW, bool PAIRS>
 __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     pdl_wait_and_release();
     using C = RcCfg<NW>;
@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(NW * 32) node_sweep_kernel(SweepParams p) {
     const bool back = (blockIdx.x & 1) != 0;
     if (q >= p.count) return;
     const SweepNode nd = p.nodes[q];
-    const int64_t n = p.pairs ? p.pairs[q].n : p.n;
-    const uint8_t *A = p.pairs ? p.pairs[q].a : p.a, *Bs = p.pairs ? p.pairs[q].b : p.b;
+    // A tree's nodes share a and b; a batch's split pairs (PAIRS) each have
+    // their own strings, no longer than p.n.
+    const int64_t n = PAIRS ? p.pairs[q].n : p.n;
+    const uint8_t *A = PAIRS ? p.pairs[q].a : p.a, *Bs = PAIRS ? p.pairs[q].b : p.b;
     int64_t i = p.pathI[nd.node], j = p.pathJ[nd.node];
     if (i < 0 || j > n || i > j || n > p.n) {             // never for a consistent tree
         if (tid == 0) set_error(p.err, ERR_BOUNDS);
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(256) node_pick_kernel(SweepParams p) {
 template <int NW>
 cudaError_t launch_sweep_t(const SweepParams &p, cudaStream_t st) {
     const size_t smem = RcCfg<NW>::bytes;
-    auto kern = node_sweep_kernel<NW>;
+    auto kern = p.pairs ? node_sweep_kernel<NW, true> : node_sweep_kernel<NW, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(kern, dim3((unsigned)(2 * p.count)), dim3(NW * 32), smem, st, p);
