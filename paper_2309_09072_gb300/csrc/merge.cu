@@ -200,21 +200,54 @@ __device__ __forceinline__ void coarse_point_cta16(const MergeParams &p, int64_t
     constexpr int PI = Fmt<int16_t>::P;
     constexpr int64_t EI = Fmt<int16_t>::ELEMS;
     const int ro = (gi & (T - 1)) * PI, co = (gj & (T - 1)) * PI;
-    int best = INT32_MIN, bk = INT32_MAX;
-#pragma unroll 2
-    for (int kb = (gi & ~3) + 4 * (int)threadIdx.x; kb <= gj; kb += 4 * (int)blockDim.x) {
-        const int64_t kt = kb >> T_SHIFT;
-        const int o = kb & (T - 1);
-        const uint2 uu = *reinterpret_cast<const uint2 *>(U + row_tile(Ib, kt, p.NT) * EI + ro + o);
-        const uint2 ll = *reinterpret_cast<const uint2 *>(L + col_tile(kt, Jb) * EI + co + o);
-        const uint32_t uw[2] = {uu.x, uu.y}, lw[2] = {ll.x, ll.y};
+    // Thread t takes offset 4 (t mod 16) of K-tiles Ib + t / 16, + 16, ..:
+    // row_tile(Ib, kt) and col_tile(kt, Jb) both grow by one tile per K-tile,
+    // so the two pointers advance by a constant.  A group of four k inside
+    // [gi, gj] is added as two packed pairs (every value there is a DIST
+    // entry in [0, 16383], so a pair's sum never carries across halves) and
+    // kept by two packed maxima, one running maximum per k mod 4; a group cut
+    // by the window's ends goes one k at a time.  Ties keep the first k of
+    // each track: the leftmost maximiser.
+    const int kl = (int)(threadIdx.x >> 4), o = 4 * (int)(threadIdx.x & 15);
+    const int64_t step = (int64_t)(blockDim.x >> 4) * EI;
+    const int16_t *up = U + row_tile(Ib, Ib + kl, p.NT) * EI + ro + o;
+    const int16_t *lp = L + col_tile(Ib + kl, Jb) * EI + co + o;
+    uint32_t bx = 0x80008000u, by = 0x80008000u;  // tracks k = 0, 1 (mod 4) and 2, 3
+    int ix0 = INT32_MAX, ix1 = INT32_MAX, iy0 = INT32_MAX, iy1 = INT32_MAX;
+    int best = INT32_MIN, bk = INT32_MAX;          // the cut groups
+    for (int64_t kt = Ib + kl; kt <= Jb; kt += blockDim.x >> 4, up += step, lp += step) {
+        const int kb = (int)(kt << T_SHIFT) + o;
+        if (kb > gj) break;
+        const uint2 uu = *reinterpret_cast<const uint2 *>(up);
+        const uint2 ll = *reinterpret_cast<const uint2 *>(lp);
+        if (kb >= gi && kb + 3 <= gj) {
+            // A halfword of the running maximum changes only where the new
+            // sum is strictly greater: its k is then the track's first.
+            const uint32_t nx = __vmaxs2(bx, uu.x + ll.x), ny = __vmaxs2(by, uu.y + ll.y);
+            const uint32_t cx = nx ^ bx, cy = ny ^ by;
+            if (cx & 0xFFFFu) ix0 = kb;
+            if (cx >> 16) ix1 = kb + 1;
+            if (cy & 0xFFFFu) iy0 = kb + 2;
+            if (cy >> 16) iy1 = kb + 3;
+            bx = nx;
+            by = ny;
+        } else {
+            const uint32_t uw[2] = {uu.x, uu.y}, lw[2] = {ll.x, ll.y};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int k = kb + e;
-            const int v = (int)(int16_t)(uw[e >> 1] >> (16 * (e & 1))) + (int)(int16_t)(lw[e >> 1] >> (16 * (e & 1)));
-            if (k >= gi && k <= gj && v > best) { best = v; bk = k; }   // k increases: first max per thread
+            for (int e = 0; e < 4; ++e) {
+                const int k = kb + e;
+                const int v = (int)(int16_t)(uw[e >> 1] >> (16 * (e & 1))) + (int)(int16_t)(lw[e >> 1] >> (16 * (e & 1)));
+                if (k >= gi && k <= gj && v > best) { best = v; bk = k; }
+            }
         }
     }
+    auto fold = [&](int v, int k) {
+        if (k != INT32_MAX && (v > best || (v == best && k < bk))) { best = v; bk = k; }
+    };
+    fold((int)(int16_t)(bx & 0xFFFFu), ix0);
+    fold((int)(int16_t)(bx >> 16), ix1);
+    fold((int)(int16_t)(by & 0xFFFFu), iy0);
+    fold((int)(int16_t)(by >> 16), iy1);
     warp_argmax(best, bk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
