@@ -199,6 +199,8 @@ struct lcs_ctx {
     int32_t schedule = LCS_SCHED_AUTO, sched_chunk = 0;
     std::vector<int64_t> sched_key;       // inputs of the current plan's schedule choice
     cudaEvent_t ev_fork = nullptr, ev_root = nullptr;
+    cudaEvent_t ev_tbl = nullptr;         // the traceback's argmax levels are done (the root tiles may start)
+    int leaf_priority = 0;                // the leaf kernel's launch priority (the device's greatest)
     // lcs_solve_host: DIST copied on a side stream while the traceback runs
     cudaStream_t side = nullptr;
     cudaEvent_t ev_dist = nullptr, ev_copied = nullptr;
@@ -291,6 +293,12 @@ lcs_status ensure_root_side(lcs_ctx *ctx) {
     if (!ctx->root_side) LCS_CK(ctx, cudaStreamCreateWithFlags(&ctx->root_side, cudaStreamNonBlocking));
     if (!ctx->ev_fork) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     if (!ctx->ev_root) LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_root, cudaEventDisableTiming));
+    if (!ctx->ev_tbl) {
+        LCS_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_tbl, cudaEventDisableTiming));
+        int least = 0, greatest = 0;
+        LCS_CK(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ctx->leaf_priority = greatest;
+    }
     return LCS_OK;
 }
 
@@ -1039,6 +1047,10 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     const bool want_len = need_len || len_dev_out;
     bool forked = false;                 // the root merge group runs on ctx->root_side
     bool fill_side = false;              // the dense fill runs on ctx->root_side
+    // The root group's tile launch, when it waits for the traceback levels.
+    bool root_deferred = false;
+    Group root_defer{};
+    MergeParams root_defer_mp{};
 
     // Degenerate grids: no rows or no columns.
     if (m == 0 || n == 0) {
@@ -1080,6 +1092,39 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
     unsigned int *sched = reinterpret_cast<unsigned int *>(base + kSchedOffset);
     if (P.dpx && P.S > 1) LCS_CK(ctx, cudaMemsetAsync(sched, 0, kSchedSlots * sizeof(unsigned int), st));
 
+    const int64_t sigma0 = coarse_sigma0(P.P);
+    int dpx_launch = 0;
+    const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
+                   : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
+    // A group's tile launch and, for the root, the dense fill and events.
+    auto tiles = [&](const Group &g, MergeParams mp, cudaStream_t gs) -> lcs_status {
+        if (P.dpx && mk != LCS_MERGE_EXACT) {
+            // A zeroed work counter per launch (zeroed above, once per solve).
+            mp.sched = dpx_launch < kSchedSlots ? sched + dpx_launch : nullptr;
+            ++dpx_launch;
+            LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                        0.0, launch_tile_dpx(mp, g.out_dt, gs));
+        } else {
+            LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
+                        0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, gs));
+            ctx->launches++;   // the pair is two kernel launches
+        }
+        if (g.root) {
+            if (!fill_side) {
+                LCS_LAUNCHK(ctx, gs, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                            launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
+                                              nullptr, gs));
+            } else if (!forked) {
+                // The early fill ran on the side stream: the DIST is
+                // complete once it has (on the side stream it precedes
+                // the root group anyway).
+                LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));
+            }
+            if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, gs));
+            if (forked) LCS_CK(ctx, cudaEventRecord(ctx->ev_root, gs));
+        }
+        return LCS_OK;
+    };
     // 1. strips
     if (P.S == 1) {
         if (dist) {
@@ -1142,8 +1187,6 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             }
         }
         // 2. merges, level by level
-        const int64_t sigma0 = coarse_sigma0(P.P);
-        int dpx_launch = 0;
         for (const Group &g : P.groups) {
             if (g.root && !dist) continue;
             // The root merge writes only the dense DIST, which the traceback
@@ -1159,8 +1202,6 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 gs = ctx->root_side;
                 forked = true;
             }
-            const int mk = ctx->merge_kernel != LCS_MERGE_AUTO ? ctx->merge_kernel
-                           : (ctx->tuned_merge >= 0 ? ctx->tuned_merge : (int)LCS_MERGE_AUTO);
             MergeParams mp{};
             mp.jobs = reinterpret_cast<const MergeJob *>(base + P.off_jobs) + g.begin;
             mp.njobs = g.count;
@@ -1176,31 +1217,18 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 mp.sigma = (int32_t)sg; mp.full = 0;
                 LCS_LAUNCHK(ctx, gs, K_COARSE, 0.0, 0.0, launch_coarse(mp, g.in_dt, gs));
             }
-            if (P.dpx && mk != LCS_MERGE_EXACT) {
-                // A zeroed work counter per launch (zeroed above, once per solve).
-                mp.sched = dpx_launch < kSchedSlots ? sched + dpx_launch : nullptr;
-                ++dpx_launch;
-                LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, launch_tile_dpx(mp, g.out_dt, gs));
-            } else {
-                LCS_LAUNCHK(ctx, gs, K_TILE, g.count * tri_entries(n) * (2.0 * dt_size(g.in_dt) + dt_size(g.out_dt)),
-                            0.0, launch_tile_pair(mp, g.in_dt, g.out_dt, gs));
-                ctx->launches++;   // the pair is two kernel launches
+            if (forked && g.root) {
+                // The root's tile launch waits for the traceback's argmax
+                // levels (below): its persistent grid fills every SM, and the
+                // leaf kernel, launched first and at a higher priority, then
+                // runs beside it instead of after it.
+                root_defer = g;
+                root_defer_mp = mp;
+                root_deferred = true;
+                continue;
             }
-            if (g.root) {
-                if (!fill_side) {
-                    LCS_LAUNCHK(ctx, gs, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
-                                launch_fill_dense(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN, 0, 0,
-                                                  nullptr, gs));
-                } else if (!forked) {
-                    // The early fill ran on the side stream: the DIST is
-                    // complete once it has (on the side stream it precedes
-                    // the root group anyway).
-                    LCS_CK(ctx, cudaStreamWaitEvent(st, ctx->ev_root, 0));
-                }
-                if (dist_ready) LCS_CK(ctx, cudaEventRecord(dist_ready, gs));
-                if (forked) LCS_CK(ctx, cudaEventRecord(ctx->ev_root, gs));
-            }
+            lcs_status ss = tiles(g, mp, gs);
+            if (ss != LCS_OK) return ss;
         }
     }
 
@@ -1215,12 +1243,18 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
             tp.len_out = nullptr; tp.root_node = P.root; tp.err = err;
             LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
         }
+        if (root_deferred) {
+            LCS_CK(ctx, cudaEventRecord(ctx->ev_tbl, st));
+            LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_tbl, 0));
+            lcs_status ss = tiles(root_defer, root_defer_mp, ctx->root_side);
+            if (ss != LCS_OK) return ss;
+        }
         LeafParams lp{};
         lp.a = a; lp.m = m; lp.h = P.h; lp.S = P.S; lp.b = b; lp.n = n;
         lp.pathI = pathI; lp.pathJ = pathJ;
         lp.vbuf = reinterpret_cast<uint32_t *>(base + P.off_vbuf);
         lp.words = P.words; lp.slots = slots; lp.counts = counts; lp.cross = cross; lp.err = err;
-        LCS_LAUNCHK(ctx, st, K_LEAF, 0.0, 0.0, launch_leaf(lp, st));
+        LCS_LAUNCHK(ctx, st, K_LEAF, 0.0, 0.0, launch_leaf(lp, st, root_deferred ? ctx->leaf_priority : 0));
         CompactParams cp{};
         cp.slots = slots; cp.counts = counts; cp.S = P.S; cp.h = P.h;
         cp.out = out_lcs; cp.cap = cap; cp.len_out = len_word(ctx); cp.len_out2 = len_dev_out; cp.err = err;
@@ -1300,6 +1334,7 @@ lcs_status lcs_destroy(lcs_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->root_side) cudaStreamDestroy(ctx->root_side);
+    if (ctx->ev_tbl) cudaEventDestroy(ctx->ev_tbl);
     if (ctx->tb_side) cudaStreamDestroy(ctx->tb_side);
     if (ctx->ev_tb_fork) cudaEventDestroy(ctx->ev_tb_fork);
     if (ctx->ev_tb) cudaEventDestroy(ctx->ev_tb);

@@ -220,7 +220,8 @@ struct LeafParams {
     int32_t *cross;       // nullable [m+1]
     int *err;
 };
-cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st);
+// priority: the launch's scheduling priority (0: the stream's).
+cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st, int priority = 0);
 
 struct CompactParams {
     const uint8_t *slots;

@@ -47,9 +47,37 @@ __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
     }
     int best = INT32_MIN;
     int64_t bk = INT64_MAX;
-    for (int64_t k = lo + threadIdx.x; k <= hi; k += blockDim.x) {
-        const int v = load_row_any(mg.U, i, k, p.NT, mg.in_dtype) + load_col_any(mg.L, k, j, mg.in_dtype);
-        if (v > best) { best = v; bk = k; }
+    if (mg.in_dtype == DT_I16) {
+        // Thread t takes four consecutive k at offset 4 (t mod 16) of K-tiles
+        // lo/T + t/16, + 16, .. (8-byte loads of U's stored row i and L's
+        // stored column j; both tiles advance by one per K-tile).
+        constexpr int PI = Fmt<int16_t>::P;
+        constexpr int64_t EI = Fmt<int16_t>::ELEMS;
+        const int16_t *U = reinterpret_cast<const int16_t *>(mg.U);
+        const int16_t *L = reinterpret_cast<const int16_t *>(mg.L);
+        const int64_t Ib = i >> T_SHIFT, Jb = j >> T_SHIFT, K0 = lo >> T_SHIFT;
+        const int kl = (int)(threadIdx.x >> 4), o = 4 * (int)(threadIdx.x & 15);
+        const int64_t step = (int64_t)(blockDim.x >> 4) * EI;
+        const int16_t *up = U + row_tile(Ib, K0 + kl, p.NT) * EI + (i & (T - 1)) * PI + o;
+        const int16_t *lp = L + col_tile(K0 + kl, Jb) * EI + (j & (T - 1)) * PI + o;
+        for (int64_t kt = K0 + kl; kt <= (hi >> T_SHIFT); kt += blockDim.x >> 4, up += step, lp += step) {
+            const int64_t kb = (kt << T_SHIFT) + o;
+            if (kb > hi) break;
+            const uint2 uu = *reinterpret_cast<const uint2 *>(up);
+            const uint2 ll = *reinterpret_cast<const uint2 *>(lp);
+            const uint32_t uw[2] = {uu.x, uu.y}, lw[2] = {ll.x, ll.y};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t k = kb + e;
+                const int v = (int)(int16_t)(uw[e >> 1] >> (16 * (e & 1))) + (int)(int16_t)(lw[e >> 1] >> (16 * (e & 1)));
+                if (k >= lo && k <= hi && v > best) { best = v; bk = k; }   // k increases: first max per thread
+            }
+        }
+    } else {
+        for (int64_t k = lo + threadIdx.x; k <= hi; k += blockDim.x) {
+            const int v = load_row_any(mg.U, i, k, p.NT, mg.in_dtype) + load_col_any(mg.L, k, j, mg.in_dtype);
+            if (v > best) { best = v; bk = k; }
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -416,21 +444,21 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_kernel(LeafParams p) {
 }
 
 template <int W>
-static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st) {
+static cudaError_t launch_leaf_t(const LeafParams &p, cudaStream_t st, int priority) {
     constexpr size_t smem = leaf_smem_layout(W).total;
     auto kern = leaf_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kern, dim3((unsigned)p.S), dim3(kLeafThreads), smem, st, p);
+    return launch_pdl_prio(kern, dim3((unsigned)p.S), dim3(kLeafThreads), smem, st, priority, p);
 }
 
-cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st) {
+cudaError_t launch_leaf(const LeafParams &p, cudaStream_t st, int priority) {
     if (p.S <= 0) return cudaSuccess;
     switch (p.words) {
-        case 1: return launch_leaf_t<1>(p, st);
-        case 2: return launch_leaf_t<2>(p, st);
-        case 4: return launch_leaf_t<4>(p, st);
-        case 8: return launch_leaf_t<8>(p, st);
+        case 1: return launch_leaf_t<1>(p, st, priority);
+        case 2: return launch_leaf_t<2>(p, st, priority);
+        case 4: return launch_leaf_t<4>(p, st, priority);
+        case 8: return launch_leaf_t<8>(p, st, priority);
         default: return cudaErrorInvalidValue;
     }
 }
