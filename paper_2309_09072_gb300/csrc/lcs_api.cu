@@ -1186,6 +1186,23 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
                 }
             }
         }
+        // A device DIST's lower triangle outside the diagonal tiles: filled on
+        // the side stream once the strips are done, beside the merge levels
+        // (bound by their (max,+) arithmetic, where the fill's HBM writes
+        // cost little), instead of after the root merge.
+        if (dist && !early_fill) {
+            lcs_status ss = ensure_root_side(ctx);
+            if (ss != LCS_OK) return ss;
+            int sms = 0;
+            LCS_CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            LCS_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+            LCS_CK(ctx, cudaStreamWaitEvent(ctx->root_side, ctx->ev_fork, 0));
+            LCS_LAUNCHK(ctx, ctx->root_side, K_FILL, tri_entries(n) * dt_size(rdt), 0.0,
+                        launch_fill_lower(dist, rdt, n, ld, rdt == DT_I16 ? INT16_MIN : INT32_MIN,
+                                          std::max(1, sms / 4), ctx->root_side));
+            LCS_CK(ctx, cudaEventRecord(ctx->ev_root, ctx->root_side));
+            fill_side = true;
+        }
         // 2. merges, level by level
         for (const Group &g : P.groups) {
             if (g.root && !dist) continue;
