@@ -275,7 +275,13 @@ cudaError_t launch_coarse(const MergeParams &p, int in_dtype, cudaStream_t st) {
         const unsigned blocks = (unsigned)(cnt * (cnt + 1) / 2 * p.njobs);
         switch (in_dtype) {
             case DT_U8: return launch_pdl(coarse_full_kernel<uint8_t>, dim3(blocks), dim3(256), 0, st, p);
-            case DT_I16: return launch_pdl(coarse_full16_kernel, dim3(blocks), dim3(256), 0, st, p);
+            case DT_I16: {
+                // A CTA per point: its fixed cost (index, reduction) is per
+                // warp, the scan's per k; short rows (n up to ~6000) take 4
+                // warps, longer ones 8.
+                const unsigned threads = p.n <= 6000 ? 128u : 256u;
+                return launch_pdl(coarse_full16_kernel, dim3(blocks), dim3(threads), 0, st, p);
+            }
             case DT_I32: return launch_pdl(coarse_full_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, p);
             default: return cudaErrorInvalidValue;
         }
