@@ -100,6 +100,10 @@ struct Plan {
     std::vector<StripOut> h_strip_outs;
     std::vector<MergeJob> h_jobs;
     std::vector<TbMerge> h_tb;
+    // Retained plans: strip s's tb merges from the root down (h_chain[s * depth_max + d], h_depth[s] of them).
+    std::vector<int32_t> h_chain, h_depth;
+    int32_t depth_max = 0;
+    size_t off_chain = 0, off_depth = 0;
 };
 
 constexpr size_t kHeaderBytes = 256;   // err word (int) at 0, length word (int64) at 8,
@@ -396,6 +400,9 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
     P.off_jobs = off; off = align256(off + sizeof(MergeJob) * std::max<size_t>(1, P.merges.size()));
     P.off_tb = off; off = align256(off + sizeof(TbMerge) * std::max<size_t>(1, P.merges.size()));
     P.off_path = off; off = align256(off + sizeof(int32_t) * 2 * P.nodes.size());
+    P.depth_max = std::max(1, P.levels);
+    P.off_chain = off; off = align256(off + sizeof(int32_t) * (size_t)P.S * P.depth_max);
+    P.off_depth = off; off = align256(off + sizeof(int32_t) * (size_t)P.S);
     P.off_counts = off; off = align256(off + sizeof(int32_t) * 2 * P.S);
     P.off_slots = off; off = align256(off + (size_t)P.S * h);
     P.off_vbuf = off; off = align256(off + (size_t)(n + P.S + 1) * P.words * 4);
@@ -438,6 +445,21 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         // group runs on a side stream): the root level scans its whole row.
         t.kgrid = (mg.out == P.root) ? nullptr : reinterpret_cast<const int32_t *>(mg.kgrid_off);
         P.h_tb[q] = t;
+    }
+    // Each strip's tb merges from the root down, for the one-launch traceback.
+    // Every pairing level puts at most one merge above a node, so no strip
+    // lies deeper than `levels` (= depth_max).
+    {
+        std::vector<int32_t> tb_of_node(P.nodes.size(), -1);
+        for (size_t q = 0; q < P.h_tb.size(); ++q) tb_of_node[P.h_tb[q].node] = (int32_t)q;
+        P.h_chain.assign((size_t)P.S * P.depth_max, 0);
+        P.h_depth.assign(P.S, 0);
+        for (int st = 0; st < P.S; ++st) {
+            std::vector<int32_t> up;
+            for (int v = st; v != P.root && P.nodes[v].parent >= 0; v = P.nodes[v].parent) up.push_back(tb_of_node[P.nodes[v].parent]);
+            P.h_depth[st] = (int32_t)std::min<size_t>(up.size(), (size_t)P.depth_max);
+            for (size_t d = 0; d < up.size() && (int)d < P.depth_max; ++d) P.h_chain[(size_t)st * P.depth_max + d] = up[up.size() - 1 - d];
+        }
     }
     P.h_jobs.resize(P.merges.size());
     for (size_t q = 0; q < P.merges.size(); ++q) {
@@ -839,6 +861,12 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb
             LCS_CK(ctx, cudaMemcpy(base + Q.off_jobs, jobs.data(), sizeof(MergeJob) * jobs.size(),
                                    cudaMemcpyHostToDevice));
             LCS_CK(ctx, cudaMemcpy(base + Q.off_tb, tb.data(), sizeof(TbMerge) * tb.size(),
+                                   cudaMemcpyHostToDevice));
+        }
+        if (!Q.h_chain.empty()) {
+            LCS_CK(ctx, cudaMemcpy(base + Q.off_chain, Q.h_chain.data(), sizeof(int32_t) * Q.h_chain.size(),
+                                   cudaMemcpyHostToDevice));
+            LCS_CK(ctx, cudaMemcpy(base + Q.off_depth, Q.h_depth.data(), sizeof(int32_t) * Q.h_depth.size(),
                                    cudaMemcpyHostToDevice));
         }
         ctx->plan_uploaded = true;
@@ -1251,14 +1279,19 @@ lcs_status solve_device(lcs_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t
 
     // 3. traceback / length
     if (want_tb || (want_len && P.S == 1)) {
-        LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_root_path(pathI, pathJ, P.root, n, st));
         const TbMerge *tbd = reinterpret_cast<const TbMerge *>(base + P.off_tb);
-        for (auto &lv : P.tb_levels) {
+        if (P.S > 1) {
+            // The splits above the leaves in one launch: a CTA per strip walks
+            // from the root down to its strip.
             TbParams tp{};
-            tp.merges = tbd + lv.first; tp.count = lv.second;
+            tp.merges = tbd; tp.count = (int32_t)P.merges.size();
             tp.n = n; tp.NT = P.NT; tp.pathI = pathI; tp.pathJ = pathJ;
             tp.len_out = nullptr; tp.root_node = P.root; tp.err = err;
-            LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_tb_level(tp, st));
+            LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0,
+                        launch_tb_path(tp, reinterpret_cast<const int32_t *>(base + P.off_chain),
+                                       reinterpret_cast<const int32_t *>(base + P.off_depth), P.depth_max, P.S, st));
+        } else {
+            LCS_LAUNCHK(ctx, st, K_TB, 0.0, 0.0, launch_root_path(pathI, pathJ, P.root, n, st));
         }
         if (root_deferred) {
             LCS_CK(ctx, cudaEventRecord(ctx->ev_tbl, st));

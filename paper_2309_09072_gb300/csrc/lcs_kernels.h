@@ -170,6 +170,10 @@ struct TbParams {
     int *err;
 };
 cudaError_t launch_tb_level(const TbParams &p, cudaStream_t st);
+// The whole traceback above the leaves in one launch: a CTA per strip takes the
+// splits of the tb merges chain[s * depth_max .. + depth[s]) from the root down.
+cudaError_t launch_tb_path(const TbParams &p, const int32_t *chain, const int32_t *depth, int32_t depth_max,
+                           int32_t strips, cudaStream_t st);
 // pathI[root] = 0, pathJ[root] = n: the whole path, source to sink.
 cudaError_t launch_root_path(int32_t *pathI, int32_t *pathJ, int32_t root, int64_t n, cudaStream_t st);
 

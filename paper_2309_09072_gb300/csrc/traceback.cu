@@ -18,18 +18,12 @@
 
 namespace lcsg {
 
-// ------------------------------------------------------------------ per-level argmax
-__global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
-    pdl_wait_and_release();
-    __shared__ int sv[8];
-    __shared__ int64_t sk[8];
-    const TbMerge mg = p.merges[blockIdx.x];
-    int64_t i = p.pathI[mg.node], j = p.pathJ[mg.node];
-    if (i < 0 || j > p.n || i > j) {          // never for a consistent tree
-        if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
-        i = 0;
-        j = 0;
-    }
+// ------------------------------------------------------------------ per-node argmax
+// The smallest maximiser c of U(i, k) + L(k, j) over i <= k <= j for merge mg,
+// and the maximum, by the whole CTA (returned to every thread).  sv, sk: a
+// slot per warp.
+__device__ void node_argmax(const TbParams &p, const TbMerge &mg, int64_t i, int64_t j, int *sv, int64_t *sk,
+                            int32_t &c_out, int &best_out) {
     // The leftmost argmax is monotone in both coordinates (Monge), so with the
     // merge's argmax grid it lies between the grid's values at the tile
     // corners around (i, j).
@@ -88,16 +82,75 @@ __global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
     __syncthreads();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (sv[w] > best || (sv[w] == best && sk[w] < bk)) { best = sv[w]; bk = sk[w]; }
+    __syncthreads();                         // sv, sk free again
+    c_out = (int32_t)bk;
+    best_out = best;
+}
+
+__global__ void __launch_bounds__(256) tb_level_kernel(TbParams p) {
+    pdl_wait_and_release();
+    __shared__ int sv[8];
+    __shared__ int64_t sk[8];
+    const TbMerge mg = p.merges[blockIdx.x];
+    int64_t i = p.pathI[mg.node], j = p.pathJ[mg.node];
+    if (i < 0 || j > p.n || i > j) {          // never for a consistent tree
+        if (threadIdx.x == 0) set_error(p.err, ERR_BOUNDS);
+        i = 0;
+        j = 0;
+    }
+    int32_t c;
+    int best;
+    node_argmax(p, mg, i, j, sv, sk, c, best);
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (sv[w] > best || (sv[w] == best && sk[w] < bk)) { best = sv[w]; bk = sk[w]; }
-        const int32_t c = (int32_t)bk;
         p.pathI[mg.upper] = (int32_t)i;
         p.pathJ[mg.upper] = c;
         p.pathI[mg.lower] = c;
         p.pathJ[mg.lower] = (int32_t)j;
         if (mg.node == p.root_node && p.len_out) *p.len_out = best;
     }
+}
+
+// One CTA per strip walks the tree from the root down to the strip, taking
+// the split of every node on its way (the upper nodes' splits are taken by
+// every CTA under them, the same values), so the whole traceback above the
+// leaves is one launch.  chain[s * depth_max + d] is the tb merge of depth d
+// on strip s's way down (depth[s] of them).
+__global__ void __launch_bounds__(256) tb_path_kernel(TbParams p, const int32_t *chain, const int32_t *depth,
+                                                      int32_t depth_max) {
+    pdl_wait_and_release();
+    __shared__ int sv[8];
+    __shared__ int64_t sk[8];
+    const int s = blockIdx.x;
+    int64_t i = 0, j = p.n;
+    const int nd = depth[s];
+    if (s == 0 && threadIdx.x == 0) {
+        p.pathI[p.root_node] = 0;            // the whole path, source to sink
+        p.pathJ[p.root_node] = (int32_t)p.n;
+    }
+    for (int d = 0; d < nd; ++d) {
+        const TbMerge mg = p.merges[chain[(int64_t)s * depth_max + d]];
+        int32_t c;
+        int best;
+        node_argmax(p, mg, i, j, sv, sk, c, best);
+        if (threadIdx.x == 0) {
+            p.pathI[mg.upper] = (int32_t)i;
+            p.pathJ[mg.upper] = c;
+            p.pathI[mg.lower] = c;
+            p.pathJ[mg.lower] = (int32_t)j;
+            if (d == 0 && p.len_out) *p.len_out = best;
+        }
+        const int32_t next = d + 1 < nd ? p.merges[chain[(int64_t)s * depth_max + d + 1]].node : s;
+        if (next == mg.upper) j = c;
+        else i = c;
+    }
+}
+
+cudaError_t launch_tb_path(const TbParams &p, const int32_t *chain, const int32_t *depth, int32_t depth_max,
+                           int32_t strips, cudaStream_t st) {
+    if (strips <= 0) return cudaSuccess;
+    return launch_pdl(tb_path_kernel, dim3((unsigned)strips), dim3(256), 0, st, p, chain, depth, depth_max);
 }
 
 __global__ void root_path_kernel(int32_t *pI, int32_t *pJ, int32_t root, int32_t n) {
