@@ -6,13 +6,15 @@
 // boundary row s between its halves is the smallest maximiser
 //     c = min argmax_{i <= k <= j} U(i, k) + L(k, j)
 // (Sec. II-D: it is a by-product of the merge), and the two halves get the
-// sub-paths (i, c) and (c, j).  tb_level_kernel resolves one tree level per
-// launch, top down.  Inside a strip (leaf) the rows are resolved directly
-// from the forward bit vectors of F(r, c) = LCS(a_strip[0:r], b[i:c]) by a
-// backward walk that keeps every row's segment as far left as it can go (see
-// leaf_kernel); letter a_r is marked when the path enters row r by a weight-1
-// diagonal (Sec. II-E).  The marked letters of all strips, in row order, are
-// the LCS.
+// sub-paths (i, c) and (c, j).  tb_path_kernel resolves every split above
+// the strips in one launch (a CTA per strip walks from the root down to its
+// strip); tb_level_kernel resolves one tree level per launch (the root level
+// alone gives the length).  Inside a strip (leaf) the rows are resolved
+// directly from the bit vectors of F(r, c) = LCS(a_strip[0:r], b[i:c]) and
+// of the backward B: the path enters row r at the smallest c with
+// F + B = L (see leaf_kernel); letter a_r is marked when the path enters row
+// r by a weight-1 diagonal (Sec. II-E).  The marked letters of all strips, in
+// row order, are the LCS.
 #include "lcs_common.cuh"
 #include "lcs_kernels.h"
 
