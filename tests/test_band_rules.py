@@ -1,0 +1,110 @@
+"""The band rules the merge and traceback kernels rest on, checked on the
+oracle's DIST merges (no GPU).
+
+For a merge D(i, j) = max_k U(i, k) + L(k, j) of two strips' DIST matrices
+(Sec. II-A, Sec. II-B-1) with K the smallest maximiser (Algorithm 2's tie
+rule), the Monge property makes K monotone in both coordinates and D is
+non-increasing in i and non-decreasing in j.  The kernels cut their work with
+three consequences, each checked here by brute force over k on tiles of a
+grid with a small tile side T (the rules do not depend on T = 64):
+
+* tile band: with kh = K at the tile's far grid corner (clipped to the tile's
+  last column) and x the largest maximiser of the near corner that is <= kh,
+  every entry (i, j) of the tile keeps a maximiser in [max(x, i), min(kh, j)]
+  and its smallest maximiser lies between the corners' K;
+* constant tiles: off the diagonal, D(far row, near column) = D(near row, far
+  column) makes D constant on the tile;
+* traceback window: K at the grid corners around (i, j) bounds K(i, j).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_09072_gb300 import inputs
+
+
+def _merge_case(seed):
+    rng = np.random.default_rng(900 + seed)
+    kind = seed % 4
+    n = int(rng.integers(24, 72))
+    m = int(rng.integers(4, 40))
+    if kind == 0:
+        a, b = inputs.random_pair(rng, m, n)
+    elif kind == 1:
+        a, b = inputs.random_pair(rng, m, n, np.frombuffer(b"AB", dtype=np.uint8))
+    elif kind == 2:
+        a, b = inputs.zipf20(rng, m), inputs.zipf20(rng, n)
+    else:
+        # correlated: b is a with substitutions and indels, so long diagonals
+        # and wide bands appear
+        a = inputs.uniform(rng, m, inputs.ACGT)
+        b = inputs.mutate(rng, a, 0.10, 0.05, inputs.ACGT, out_len=n)
+    s = int(rng.integers(1, m))
+    U = oracle.dist(a[:s], b).astype(np.int64)
+    L = oracle.dist(a[s:], b).astype(np.int64)
+    D, K = oracle.merge(U, L)
+    return n, U, L, D.astype(np.int64), K.astype(np.int64)
+
+
+def _grid(T, n):
+    P = -(-n // T)
+    return P, [min(p * T, n) for p in range(P + 1)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("T", [3, 4, 8])
+def test_tile_band_keeps_a_maximiser(seed, T):
+    n, U, L, D, K = _merge_case(seed)
+    P, g = _grid(T, n)
+    for I in range(P):
+        for J in range(I, P):
+            ia, ja = g[I], g[J]
+            rows = range(ia, min(ia + T, n + 1))
+            cols = range(ja, min(ja + T, n + 1))
+            k_near, k_far = K[g[I], g[J]], K[g[I + 1], g[J + 1]]
+            kh = min(k_far, ja + T - 1)
+            near = [k for k in range(ia, ja + 1) if k <= kh and U[ia, k] + L[k, ja] == D[ia, ja]]
+            assert near, "the near corner's maximisers reach below the far corner's"
+            x = max(near)
+            for i in rows:
+                for j in cols:
+                    if i > j:
+                        continue
+                    assert k_near <= K[i, j] <= k_far
+                    lo, hi = max(x, i), min(kh, j)
+                    assert lo <= hi
+                    best = max(U[i, k] + L[k, j] for k in range(lo, hi + 1))
+                    assert best == D[i, j], (I, J, i, j)
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("T", [2, 4, 8])
+def test_constant_tiles(seed, T):
+    n, U, L, D, K = _merge_case(seed)
+    P, g = _grid(T, n)
+    constant = 0
+    for I in range(P):
+        for J in range(I + 1, P):
+            vmin, vmax = D[g[I + 1], g[J]], D[g[I], g[J + 1]]
+            tile = D[g[I]:min(g[I] + T, n + 1), g[J]:min(g[J] + T, n + 1)]
+            assert tile.min() >= vmin and tile.max() <= vmax
+            if vmin == vmax:
+                constant += 1
+                assert np.all(tile == vmax)
+    # the rule is exercised, not vacuous, on the cases with long b
+    if n >= 48 and T == 2:
+        assert constant > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("T", [4, 8])
+def test_traceback_window_from_grid_corners(seed, T):
+    n, U, L, D, K = _merge_case(seed)
+    P, g = _grid(T, n)
+    for i in range(n + 1):
+        for j in range(i, n + 1):
+            I0, J0 = min(i // T, P), min(j // T, P)
+            I1, J1 = min(I0 + 1, P), min(J0 + 1, P)
+            lo = max(i, K[g[I0], g[J0]])
+            hi = min(j, K[g[I1], g[J1]])
+            assert lo <= K[i, j] <= hi
