@@ -1,5 +1,5 @@
-"""The band rules the merge and traceback kernels rest on, checked on the
-oracle's DIST merges (no GPU).
+"""The rules the merge and traceback kernels rest on, checked against the
+oracle on small inputs (no GPU).
 
 For a merge D(i, j) = max_k U(i, k) + L(k, j) of two strips' DIST matrices
 (Sec. II-A, Sec. II-B-1) with K the smallest maximiser (Algorithm 2's tie
@@ -15,6 +15,14 @@ grid with a small tile side T (the rules do not depend on T = 64):
 * constant tiles: off the diagonal, D(far row, near column) = D(near row, far
   column) makes D constant on the tile;
 * traceback window: K at the grid corners around (i, j) bounds K(i, j).
+
+The leaf traceback (Sec. II-C, II-E) takes a strip's part of the path, from
+(0, i) to (h, j), without a DP table of pointers: with F(r, c) =
+LCS(a[0:r], b[i:c]) and B(r, c) = LCS(a[r:h], b[c:j]) the vertices on
+heaviest paths are those with F + B = L = F(h, j), the leftmost heaviest path
+enters row r at v[r] = min{c : F(r, c) + B(r, c) = L}, and letter a_r is on
+the LCS exactly when v[r] > v[r-1] and a_r = b_{v[r]}.  That is checked
+against the oracle's leftmost traceback of the same strip and segment.
 """
 import numpy as np
 import pytest
@@ -108,3 +116,25 @@ def test_traceback_window_from_grid_corners(seed, T):
             lo = max(i, K[g[I0], g[J0]])
             hi = min(j, K[g[I1], g[J1]])
             assert lo <= K[i, j] <= hi
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_leaf_rule_matches_leftmost_traceback(seed):
+    rng = np.random.default_rng(950 + seed)
+    alph = [inputs.ACGT, np.frombuffer(b"AB", dtype=np.uint8), inputs.AA20][seed % 3]
+    for _ in range(30):
+        h = int(rng.integers(1, 12))
+        n = int(rng.integers(0, 16))
+        a, b = inputs.random_pair(rng, h, n, alph)
+        i = int(rng.integers(0, n + 1))
+        j = int(rng.integers(i, n + 1))
+        F = np.array([[oracle.lcs_length(a[:r], b[i:c]) for c in range(i, j + 1)] for r in range(h + 1)])
+        B = np.array([[oracle.lcs_length(a[r:], b[c:j]) for c in range(i, j + 1)] for r in range(h + 1)])
+        L = F[h, j - i]
+        assert B[0, 0] == L
+        v = [int(np.flatnonzero(F[r] + B[r] == L)[0]) for r in range(h + 1)]
+        marked = bytes(int(a[r - 1]) for r in range(1, h + 1)
+                       if v[r] > v[r - 1] and a[r - 1] == b[i + v[r] - 1])
+        s_ref, v_ref = oracle.traceback(a, b[i:j])
+        assert [int(x) for x in v_ref] == v
+        assert marked == s_ref
