@@ -23,6 +23,14 @@ heaviest paths are those with F + B = L = F(h, j), the leftmost heaviest path
 enters row r at v[r] = min{c : F(r, c) + B(r, c) = L}, and letter a_r is on
 the LCS exactly when v[r] > v[r-1] and a_r = b_{v[r]}.  That is checked
 against the oracle's leftmost traceback of the same strip and segment.
+
+The strip builder holds F_j(r) = LCS(a[0:r], b[i:j]) for one source i as an
+h-bit vector whose zero bits mark the rows where F steps up, advanced by the
+bit-vector step u = V & M, V' = (V + u) | (V & ~M) (Allison-Dix / Hyyro) with
+the carry out of the top row the increment of DIST(i, j).  It skips the low
+words once they are zero: the first r rows have all stepped exactly when
+a[0:r] is a subsequence of b[i:j], zero words stay zero, and a step started
+at the first live word with no carry in gives the same vector and carry.
 """
 import numpy as np
 import pytest
@@ -138,3 +146,56 @@ def test_leaf_rule_matches_leftmost_traceback(seed):
         s_ref, v_ref = oracle.traceback(a, b[i:j])
         assert [int(x) for x in v_ref] == v
         assert marked == s_ref
+
+
+def _is_subsequence(s, t):
+    it = iter(bytes(t))
+    return all(ch in it for ch in bytes(s))
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("word", [4, 8, 32])
+def test_strip_vector_and_settled_words(seed, word):
+    rng = np.random.default_rng(970 + seed)
+    alph = [inputs.ACGT, np.frombuffer(b"AB", dtype=np.uint8), inputs.AA20][seed % 3]
+    h = int(rng.integers(1, 41))
+    n = int(rng.integers(0, 60))
+    a, b = inputs.random_pair(rng, h, n, alph)
+    if seed % 2:
+        b = inputs.mutate(rng, np.tile(a, 3), 0.1, 0.05, alph, out_len=n)
+    D = oracle.dist(a, b).astype(np.int64)
+    full = (1 << h) - 1
+    M = {int(c): sum(1 << r for r in range(h) if a[r] == c) for c in set(a.tolist()) | set(b.tolist())}
+    words = -(-h // word)
+    wmask = (1 << word) - 1
+    for i in range(n + 1):
+        V, d, settled = full, 0, 0
+        for j in range(i + 1, n + 1):
+            m = M[int(b[j - 1])]
+            u = V & m
+            tot = V + u
+            carry = tot >> h
+            Vn = (tot | (V & ~m)) & full
+            # the same step from the first live word S on, no carry in
+            S = settled
+            lo = S * word
+            tot_s = (V >> lo) + (u >> lo)
+            assert (tot_s >> (h - lo)) == carry
+            assert ((tot_s | ((V & ~m) >> lo)) & (full >> lo)) << lo == Vn
+            V = Vn
+            d += carry
+            assert d == D[i, j]
+            zeros = [r for r in range(h) if not (V >> r) & 1]
+            # F_j(r) = number of zero bits among rows 0..r-1
+            for r in range(h + 1):
+                assert sum(1 for z in zeros if z < r) == oracle.lcs_length(a[:r], b[i:j])
+            # low words zero <=> that prefix of a is a subsequence of b[i:j]
+            now = 0
+            while now < words and ((V >> (now * word)) & wmask) == 0:
+                now += 1
+            for w in range(words):
+                rows = min((w + 1) * word, h)
+                low_zero = (V & ((1 << rows) - 1)) == 0
+                assert low_zero == _is_subsequence(a[:rows], b[i:j])
+            assert now >= settled          # zero words stay zero
+            settled = now
