@@ -181,6 +181,67 @@ lcs_status lcs_set_fault_injection(lcs_ctx *ctx, int32_t hold_band, int64_t wait
 enum { LCS_SCHED_AUTO = 0, LCS_SCHED_RETAIN = 1, LCS_SCHED_DEPTH = 2 };
 lcs_status lcs_set_schedule(lcs_ctx *ctx, int32_t mode, int32_t chunk);
 
+/* The tree plan of a solve that writes DIST (Sec. II-A: strips of h rows of
+ * a, combined pairwise up a binary tree of (max,+) merges), as lcs_plan
+ * reports it. */
+typedef struct {
+    int64_t workspace_bytes;   /* device workspace the plan needs (the caller's
+                                  outputs not counted)                        */
+    int32_t fits;              /* 1: workspace_bytes is within budget_bytes;
+                                  0: a solve would return ENOMEM             */
+    int32_t strip_height;      /* h                                          */
+    int32_t strips;            /* S = ceil(m / h); 0 when m or n is 0        */
+    int32_t nodes;             /* 2S - 1 (strips, then merge outputs)        */
+    int32_t levels;            /* merges on the longest strip-to-root chain  */
+    int32_t depth_first;       /* 0: retained tree, 1: depth first           */
+    int32_t chunk;             /* strips per strip launch                    */
+    int32_t launches;          /* strip launches + merge-group launches      */
+    int32_t root;              /* node id of the root                        */
+    int32_t tile;              /* merge tile edge (vertices)                 */
+} lcs_plan_info;
+
+/* One node of the plan.  Node ids: strips 0 .. S-1 in row order, then the
+ * merge outputs.  Launches are numbered 0 .. launches-1 in stream order. */
+typedef struct {
+    int64_t row0, rows;        /* the rows of a the node covers              */
+    int64_t offset, bytes;     /* its stored triangle in the workspace (0, 0
+                                  for the root: the caller's matrix)         */
+    int64_t grid_offset, grid_bytes;  /* merge outputs: the merge's argmax and
+                                  value grids in the workspace (0, 0 for
+                                  strips)                                    */
+    int32_t upper, lower;      /* children (merge outputs; -1 for strips)    */
+    int32_t parent;            /* -1 for the root                            */
+    int32_t level;             /* 0 for strips, else 1 + the children's      */
+    int32_t made_by;           /* the launch that writes it                  */
+    int32_t last_use;          /* the last launch of the tree that needs its
+                                  storage (the merge that consumes it when
+                                  depth first; `launches` when the tree is
+                                  retained for the traceback)                */
+    int32_t grid_last_use;     /* the same for its grids (depth first: the
+                                  launch that makes it; they are reused by
+                                  later launches)                            */
+} lcs_plan_node;
+
+/* Host only: no device, no context, no CUDA call.  The plan a solve of an
+ * m x n pair would use for its tree, chosen as lcs_solve chooses it: h (0:
+ * the automatic strip height), `schedule` and `chunk` as lcs_set_schedule
+ * takes them, budget_bytes as lcs_create takes mem_budget_bytes (0: 64
+ * GiB), want_lcs (1: the solve also wants an LCS, which keeps the retained
+ * tree when a tree half would exceed 16384 rows), root_dtype the dtype of
+ * the DIST output.  Fills *info and the first min(cap, info->nodes) node
+ * records (nodes may be NULL when cap is 0).  For sizing a budget before
+ * lcs_create and for checking the schedule: the storage of nodes alive
+ * during a launch (made_by <= launch <= last_use) and the grids in use
+ * (made_by <= launch <= grid_last_use) never share workspace bytes.  A
+ * context that holds host-call staging (lcs_solve_host) has that much less
+ * of its budget for the workspace.
+ * Errors: EINVAL (negative lengths, h outside 0..256, an unknown schedule,
+ * chunk < 0, a bad dtype, LCS_I16 with m or n >= 32768, info NULL, cap < 0,
+ * nodes NULL with cap > 0). */
+lcs_status lcs_plan(int64_t m, int64_t n, int32_t h, int32_t schedule, int32_t chunk, size_t budget_bytes,
+                    int32_t want_lcs, lcs_dtype root_dtype, lcs_plan_info *info, lcs_plan_node *nodes,
+                    int64_t cap);
+
 /* CUDA-graph replay of lcs_solve (1) or plain launches (0, the default).
  * With graphs on, the first lcs_solve with a given set of arguments runs as
  * usual and is then captured (on a private stream) into a graph; later

@@ -53,6 +53,40 @@ class lcs_kernel_profile(ctypes.Structure):
     ]
 
 
+class lcs_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("workspace_bytes", ctypes.c_int64),
+        ("fits", ctypes.c_int32),
+        ("strip_height", ctypes.c_int32),
+        ("strips", ctypes.c_int32),
+        ("nodes", ctypes.c_int32),
+        ("levels", ctypes.c_int32),
+        ("depth_first", ctypes.c_int32),
+        ("chunk", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("root", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+    ]
+
+
+class lcs_plan_node(ctypes.Structure):
+    _fields_ = [
+        ("row0", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("offset", ctypes.c_int64),
+        ("bytes", ctypes.c_int64),
+        ("grid_offset", ctypes.c_int64),
+        ("grid_bytes", ctypes.c_int64),
+        ("upper", ctypes.c_int32),
+        ("lower", ctypes.c_int32),
+        ("parent", ctypes.c_int32),
+        ("level", ctypes.c_int32),
+        ("made_by", ctypes.c_int32),
+        ("last_use", ctypes.c_int32),
+        ("grid_last_use", ctypes.c_int32),
+    ]
+
+
 LCS_WANT_STRING = 1
 
 
@@ -114,6 +148,8 @@ def load(path: str = LIB_PATH):
             "lcs_set_graphs": ([vp, i32], st),
             "lcs_set_fault_injection": ([vp, i32, i64], st),
             "lcs_set_schedule": ([vp, i32, i32], st),
+            "lcs_plan": ([i64, i64, i32, i32, i32, sz, i32, st, ctypes.POINTER(lcs_plan_info),
+                          ctypes.POINTER(lcs_plan_node), i64], st),
             "lcs_autotune": ([vp, vp, i64, vp, i64, i32, vp, i64, vp, i64, vp, ctypes.POINTER(i32),
                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)], st),
             "lcs_get_stats": ([vp, ctypes.POINTER(lcs_stats)], st),
@@ -261,6 +297,25 @@ LCS_SCHED_AUTO, LCS_SCHED_RETAIN, LCS_SCHED_DEPTH = 0, 1, 2
 
 def lcs_set_schedule(ctx, mode: int, chunk: int = 0) -> None:
     _check(ctx, load().lcs_set_schedule(ctx, int(mode), int(chunk)))
+
+
+def lcs_plan(m: int, n: int, h: int = 0, schedule: int = LCS_SCHED_AUTO, chunk: int = 0, budget_bytes: int = 0,
+             want_lcs: bool = True, dtype: int = LCS_I32):
+    """The tree plan a solve of an m x n pair would use (host only, no
+    device): (info dict, list of node dicts)."""
+    lib = load()
+    info = lcs_plan_info()
+    st = lib.lcs_plan(int(m), int(n), int(h), int(schedule), int(chunk), int(budget_bytes), 1 if want_lcs else 0,
+                      int(dtype), ctypes.byref(info), None, 0)
+    if st != LCS_OK:
+        raise LcsError(st, "lcs_plan arguments")
+    recs = (lcs_plan_node * max(1, info.nodes))()
+    st = lib.lcs_plan(int(m), int(n), int(h), int(schedule), int(chunk), int(budget_bytes), 1 if want_lcs else 0,
+                      int(dtype), ctypes.byref(info), recs, int(info.nodes))
+    if st != LCS_OK:
+        raise LcsError(st, "lcs_plan arguments")
+    nodes = [{name: getattr(recs[v], name) for name, _ in lcs_plan_node._fields_} for v in range(info.nodes)]
+    return {name: getattr(info, name) for name, _ in info._fields_}, nodes
 
 
 def lcs_set_fault_injection(ctx, hold_band: bool, wait_limit_ns: int = 0) -> None:

@@ -50,6 +50,7 @@ struct Node {
     int parent = -1;
     bool root = false;
     size_t off = 0;        // storage offset in the workspace (non-root nodes)
+    size_t bytes = 0;      // its stored triangle (non-root nodes)
 };
 
 struct Merge {
@@ -390,7 +391,8 @@ Plan build_plan(int64_t m, int64_t n, int h, int root_dt) {
         Node &nd = P.nodes[v];
         if (nd.root) continue;
         nd.off = off;
-        off = align256(off + (size_t)tiles * tile_elems(nd.dtype) * dt_size(nd.dtype));
+        nd.bytes = (size_t)tiles * tile_elems(nd.dtype) * dt_size(nd.dtype);
+        off = align256(off + nd.bytes);
     }
     for (auto &mg : P.merges) {
         mg.kgrid_off = off;                       // kgrid then vgrid
@@ -627,8 +629,12 @@ Plan build_plan_depth_first(int64_t m, int64_t n, int h, int root_dt, int chunk)
     size_t off = kHeaderBytes;
     const size_t pool = off;
     off += (size_t)nslots * slot_bytes;
-    for (size_t v = 0; v < P.nodes.size(); ++v)
-        if (!P.nodes[v].root) P.nodes[v].off = pool + (size_t)slot[v] * slot_bytes;
+    for (size_t v = 0; v < P.nodes.size(); ++v) {
+        Node &nd = P.nodes[v];
+        if (nd.root) continue;
+        nd.off = pool + (size_t)slot[v] * slot_bytes;
+        nd.bytes = (size_t)num_tiles_tri(P.NT) * tile_elems(nd.dtype) * dt_size(nd.dtype);
+    }
     // Coarse grids: one per merge of the largest group, reused group after group.
     const size_t kg_bytes = align256(2 * (size_t)(P.P + 1) * (P.P + 1) * 4);
     const size_t kg_base = off;
@@ -745,14 +751,21 @@ lcs_status ensure_io(lcs_ctx *ctx, size_t bytes) {
 // the dominant cost, so at m = n = 4096 the autotuner's candidates 64, 128
 // and 256 rank in that order, slowest first.  A smaller h set by the caller
 // is doubled while the retained tree would not fit the budget.
-int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
+// `room`: the budget left for the workspace.
+int pick_strip_height(int64_t m, int64_t n, int root_dt, size_t room) {
     int h = auto_strip_height(m, n);
     while (h < 256 && m > h) {
         const Plan q = build_plan(m, n, h, root_dt);
-        if (q.total + ctx->io_bytes <= ctx->budget) break;
+        if (q.total <= room) break;
         h *= 2;
     }
     return h;
+}
+
+size_t room_of(const lcs_ctx *ctx) { return ctx->budget > ctx->io_bytes ? ctx->budget - ctx->io_bytes : 0; }
+
+int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
+    return pick_strip_height(m, n, root_dt, room_of(ctx));
 }
 
 // Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
@@ -771,25 +784,25 @@ std::vector<int64_t> tune_key(int64_t m, int64_t n, int root_dt) {
 // traceback sweeps a tree half of at most sweep_max_rows() rows in one CTA,
 // so a taller half keeps the retained tree when an LCS is wanted.
 constexpr size_t kRetainLimit = (size_t)4 << 30;
+constexpr size_t kDefaultBudget = (size_t)64 << 30;   // lcs_create's mem_budget_bytes = 0
 constexpr size_t kDepthTarget = (size_t)16 << 30;
 
-Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool want_tb) {
+Plan pick_plan(int schedule, int sched_chunk, size_t room, int64_t m, int64_t n, int h, int root_dt, bool want_tb) {
     Plan R = build_plan(m, n, h, root_dt);
-    if (ctx->schedule == LCS_SCHED_RETAIN || R.S <= 1) return R;
-    const size_t room = ctx->budget > ctx->io_bytes ? ctx->budget - ctx->io_bytes : 0;
-    if (ctx->schedule == LCS_SCHED_AUTO && R.total <= std::min(room, kRetainLimit)) return R;
+    if (schedule == LCS_SCHED_RETAIN || R.S <= 1) return R;
+    if (schedule == LCS_SCHED_AUTO && R.total <= std::min(room, kRetainLimit)) return R;
     auto too_tall = [&](const Plan &D) {
         for (auto &mg : D.merges)
             if (std::max(D.nodes[mg.u].rows, D.nodes[mg.l].rows) > sweep_max_rows()) return true;
         return false;
     };
     std::vector<int> chunks;
-    if (ctx->sched_chunk > 0) chunks.push_back(ctx->sched_chunk);
+    if (sched_chunk > 0) chunks.push_back(sched_chunk);
     else chunks = {32, 16, 8, 4, 2, 1};
-    const size_t target = ctx->sched_chunk > 0 ? room : std::min(room, kDepthTarget);
+    const size_t target = sched_chunk > 0 ? room : std::min(room, kDepthTarget);
     Plan D;
     for (int c : chunks) {
-        if (c > R.S && c > 1 && ctx->sched_chunk == 0) continue;
+        if (c > R.S && c > 1 && sched_chunk == 0) continue;
         D = build_plan_depth_first(m, n, h, root_dt, c);
         if (want_tb && too_tall(D)) return R;
         if (D.total <= target) return D;
@@ -797,6 +810,10 @@ Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool wa
     // Nothing within the target: the smallest chunk that fits the budget.
     if (D.total <= room) return D;
     return R.total <= room ? R : D;      // neither fits: ensure_workspace reports ENOMEM
+}
+
+Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool want_tb) {
+    return pick_plan(ctx->schedule, ctx->sched_chunk, room_of(ctx), m, n, h, root_dt, want_tb);
 }
 
 lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb) {
@@ -1360,7 +1377,7 @@ lcs_status lcs_create(lcs_ctx **out, int device, size_t mem_budget_bytes) {
     lcs_ctx *ctx = new (std::nothrow) lcs_ctx();
     if (!ctx) return LCS_ENOMEM;
     ctx->device = device;
-    ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)64 << 30;
+    ctx->budget = mem_budget_bytes ? mem_budget_bytes : kDefaultBudget;
     *out = ctx;
     return LCS_OK;
 }
@@ -1430,6 +1447,96 @@ lcs_status lcs_set_schedule(lcs_ctx *ctx, int32_t mode, int32_t chunk) {
         return fail(ctx, LCS_EINVAL, "schedule arguments");
     ctx->schedule = mode;
     ctx->sched_chunk = chunk;
+    return LCS_OK;
+}
+
+lcs_status lcs_plan(int64_t m, int64_t n, int32_t h, int32_t schedule, int32_t chunk, size_t budget_bytes,
+                    int32_t want_lcs, lcs_dtype root_dtype, lcs_plan_info *info, lcs_plan_node *nodes,
+                    int64_t cap) {
+    if (!info || m < 0 || n < 0 || h < 0 || h > 256 || schedule < LCS_SCHED_AUTO || schedule > LCS_SCHED_DEPTH ||
+        chunk < 0 || cap < 0 || (cap > 0 && !nodes))
+        return LCS_EINVAL;
+    if (n >= INT32_MAX / 2 || m >= INT32_MAX / 2) return LCS_EINVAL;
+    if (root_dtype != LCS_I32 && root_dtype != LCS_I16) return LCS_EINVAL;
+    if (root_dtype == LCS_I16 && (m >= 32768 || n >= 32768)) return LCS_EINVAL;
+    *info = lcs_plan_info{};
+    info->tile = T;
+    info->root = -1;
+    const size_t budget = budget_bytes ? budget_bytes : kDefaultBudget;
+    if (m == 0 || n == 0) {
+        // No tree: the solve writes the degenerate DIST and length directly.
+        info->workspace_bytes = (int64_t)kHeaderBytes;
+        info->fits = kHeaderBytes <= budget ? 1 : 0;
+        return LCS_OK;
+    }
+    const int rdt = api_dt(root_dtype);
+    if (h == 0) h = pick_strip_height(m, n, rdt, budget);
+    const Plan P = pick_plan(schedule, chunk, budget, m, n, h, rdt, want_lcs != 0);
+    // Launches in stream order: the retained tree builds every strip in one
+    // launch and then launches each merge group; the depth-first plan runs
+    // its steps.
+    std::vector<int32_t> made(P.nodes.size(), -1), last(P.nodes.size(), -1);
+    int32_t launches = 0;
+    auto group_launch = [&](const Group &g, int32_t L) {
+        for (int q = g.begin; q < g.begin + g.count; ++q) {
+            const Merge &mg = P.merges[q];
+            made[mg.out] = L;
+            last[mg.u] = L;
+            last[mg.l] = L;
+        }
+    };
+    if (P.depth_first) {
+        for (const Step &st : P.steps) {
+            if (st.strips) {
+                for (int s = st.begin; s < st.begin + st.count; ++s) made[s] = launches;
+            } else {
+                group_launch(P.groups[st.begin], launches);
+            }
+            ++launches;
+        }
+    } else {
+        for (int s = 0; s < P.S; ++s) made[s] = 0;
+        launches = 1;
+        for (const Group &g : P.groups) group_launch(g, launches++);
+        for (auto &x : last) x = launches;   // every node is kept for the traceback
+    }
+    if (P.root >= 0) last[P.root] = launches;
+    info->workspace_bytes = (int64_t)P.total;
+    info->fits = P.total <= budget ? 1 : 0;
+    info->strip_height = P.h;
+    info->strips = P.S;
+    info->nodes = (int32_t)P.nodes.size();
+    info->levels = P.levels;
+    info->depth_first = P.depth_first ? 1 : 0;
+    info->chunk = P.depth_first ? P.chunk : P.S;
+    info->launches = launches;
+    info->root = P.root;
+    const int64_t count = std::min<int64_t>(cap, (int64_t)P.nodes.size());
+    for (int64_t v = 0; v < count; ++v) {
+        const Node &nd = P.nodes[v];
+        lcs_plan_node r{};
+        r.row0 = nd.row0;
+        r.rows = nd.rows;
+        r.offset = nd.root ? 0 : (int64_t)nd.off;
+        r.bytes = nd.root ? 0 : (int64_t)nd.bytes;
+        r.upper = r.lower = -1;
+        r.parent = nd.parent;
+        r.level = nd.level;
+        r.made_by = made[v];
+        r.last_use = last[v];
+        r.grid_last_use = -1;
+        nodes[v] = r;
+    }
+    const int64_t grid_bytes = 2 * (int64_t)(P.P + 1) * (P.P + 1) * 4;   // argmax grid, then value grid
+    for (const Merge &mg : P.merges) {
+        if (mg.out >= count) continue;
+        lcs_plan_node &r = nodes[mg.out];
+        r.upper = mg.u;
+        r.lower = mg.l;
+        r.grid_offset = (int64_t)mg.kgrid_off;
+        r.grid_bytes = grid_bytes;
+        r.grid_last_use = P.depth_first ? made[mg.out] : launches;
+    }
     return LCS_OK;
 }
 

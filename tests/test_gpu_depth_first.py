@@ -57,6 +57,11 @@ def test_chunks_and_tree_shapes(ctx, chunk):
             a, b = inputs.random_pair(rng, m, n, ALPH2 if m % 2 else inputs.ACGT)
             r = solve(ctx, a, b, h=h)
             assert r["stats"]["depth_first"] == 1
+            # the host-only plan query reports the plan the solve used
+            info, _ = B.lcs_plan(m, n, h, B.LCS_SCHED_DEPTH, chunk, want_lcs=True)
+            st = r["stats"]
+            assert (st["plan_bytes"], st["chunk_strips"], st["strips"], st["tree_levels"]) == (
+                info["workspace_bytes"], info["chunk"], info["strips"], info["levels"])
             s_want, v_want = oracle.traceback(a, b)
             assert r["L"] == len(s_want) and r["s"] == s_want and np.array_equal(r["cross"], v_want)
             assert np.array_equal(r["D"], oracle_dist(a, b))
@@ -100,6 +105,8 @@ def test_small_budget_uses_depth_first():
         solve(big, a, b, h=128, want_lcs=False)
         retained = B.lcs_get_stats(big)
         assert retained["depth_first"] == 0
+        info, _ = B.lcs_plan(len(a), len(b), 128, want_lcs=False)
+        assert info["depth_first"] == 0 and info["workspace_bytes"] == retained["plan_bytes"]
     finally:
         B.lcs_destroy(big)
     budget = retained["plan_bytes"] // 3
@@ -108,6 +115,9 @@ def test_small_budget_uses_depth_first():
         r = solve(c, a, b, h=128)
         assert r["stats"]["depth_first"] == 1
         assert r["stats"]["peak_workspace_bytes"] <= budget
+        info, _ = B.lcs_plan(len(a), len(b), 128, B.LCS_SCHED_AUTO, 0, budget, want_lcs=True)
+        assert info["depth_first"] == 1 and info["fits"] == 1
+        assert (info["workspace_bytes"], info["chunk"]) == (r["stats"]["plan_bytes"], r["stats"]["chunk_strips"])
         s_want, v_want = oracle.traceback(a, b)
         assert r["L"] == len(s_want) and r["s"] == s_want and np.array_equal(r["cross"], v_want)
         assert np.array_equal(r["D"], oracle.dist(a, b))
