@@ -314,6 +314,11 @@ lcs_status ensure_tb_side(lcs_ctx *ctx) {
     return LCS_OK;
 }
 
+// Strip height when none is set: 256 rows (eight 32-bit words per bit
+// vector), or m for a shorter a.  Halving h doubles the strips but adds a
+// tree level of merges, the dominant cost, so at m = n = 4096 the
+// autotuner's candidates 64, 128 and 256 rank in that order, slowest first.
+// Memory is bounded by the schedule (depth first), not by the strip height.
 int auto_strip_height(int64_t m, int64_t n) {
     (void)n;
     if (m <= 256) return (int)std::max<int64_t>(m, 1);
@@ -746,29 +751,9 @@ lcs_status ensure_io(lcs_ctx *ctx, size_t bytes) {
     return LCS_OK;
 }
 
-// Strip height when none is set: 256 rows (eight 32-bit words per bit
-// vector).  Halving h doubles the strips but adds a tree level of merges,
-// the dominant cost, so at m = n = 4096 the autotuner's candidates 64, 128
-// and 256 rank in that order, slowest first.  A smaller h set by the caller
-// is doubled while the retained tree would not fit the budget.
-// `room`: the budget left for the workspace.
-int pick_strip_height(int64_t m, int64_t n, int root_dt, size_t room) {
-    int h = auto_strip_height(m, n);
-    while (h < 256 && m > h) {
-        const Plan q = build_plan(m, n, h, root_dt);
-        if (q.total <= room) break;
-        h *= 2;
-    }
-    return h;
-}
-
+// The budget left for the workspace (host-call staging holds the rest).
 size_t room_of(const lcs_ctx *ctx) { return ctx->budget > ctx->io_bytes ? ctx->budget - ctx->io_bytes : 0; }
 
-int choose_strip_height(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt) {
-    return pick_strip_height(m, n, root_dt, room_of(ctx));
-}
-
-// Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
 // Size bucket of the autotuner: floor(log2) of each length and the root
 // dtype (the dense output, when asked for, changes the root merge's work).
 std::vector<int64_t> tune_key(int64_t m, int64_t n, int root_dt) {
@@ -816,6 +801,7 @@ Plan choose_plan(lcs_ctx *ctx, int64_t m, int64_t n, int h, int root_dt, bool wa
     return pick_plan(ctx->schedule, ctx->sched_chunk, room_of(ctx), m, n, h, root_dt, want_tb);
 }
 
+// Make ctx->plan match (m, n, h, root dtype) and upload its device arrays.
 lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb) {
     Plan &P = ctx->plan;
     int h = ctx->strip_h;
@@ -829,7 +815,7 @@ lcs_status prepare(lcs_ctx *ctx, int64_t m, int64_t n, int root_dt, bool want_tb
             ctx->tuned_merge = it->second.second;
         } else {
             h = (P.m == m && P.n == n && P.root_dt == root_dt && ctx->auto_h) ? P.h
-                                                                               : choose_strip_height(ctx, m, n, root_dt);
+                                                                               : auto_strip_height(m, n);
         }
         ctx->auto_h = true;
     } else {
@@ -1470,7 +1456,7 @@ lcs_status lcs_plan(int64_t m, int64_t n, int32_t h, int32_t schedule, int32_t c
         return LCS_OK;
     }
     const int rdt = api_dt(root_dtype);
-    if (h == 0) h = pick_strip_height(m, n, rdt, budget);
+    if (h == 0) h = auto_strip_height(m, n);
     const Plan P = pick_plan(schedule, chunk, budget, m, n, h, rdt, want_lcs != 0);
     // Launches in stream order: the retained tree builds every strip in one
     // launch and then launches each merge group; the depth-first plan runs
